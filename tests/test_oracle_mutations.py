@@ -62,11 +62,11 @@ def test_window_mutants_fail(monkeypatch, name):
     assert not _nfft_pin()
 
 
-@pytest.mark.parametrize("mutant", ["shifted_points", "wrong_e0", "degree_M"])
+@pytest.mark.parametrize("mutant", ["scaled_points", "wrong_e0", "degree_M"])
 def test_weight_mutants_fail(monkeypatch, mutant):
-    if mutant == "shifted_points":
+    if mutant == "scaled_points":
         orig = WT.matrix_A
-        monkeypatch.setattr(WT, "matrix_A", lambda x, M: orig(x + 0.01, M))
+        monkeypatch.setattr(WT, "matrix_A", lambda x, M: orig(1.01 * x, M))
     elif mutant == "wrong_e0":
         orig = WT.e0
         monkeypatch.setattr(WT, "e0", lambda M2, d: np.roll(orig(M2, d), 1))
