@@ -1,0 +1,209 @@
+/*
+ * infft.h -- C ABI of a GB300 (sm_103a) library for the direct inverse NFFT
+ * of Kircheis & Potts, "Fast and direct inversion methods for the
+ * multivariate nonequispaced fast Fourier transform".
+ *
+ * Notation (Section 2): d in {1,2,3}; M even; I_M = Z^d cap [-M/2, M/2)^d;
+ * points x_j in the torus T^d = [-1/2, 1/2)^d, j = 1..N; A = (exp(2 pi i k x_j))
+ * (eq. matrix_A); M_sigma = 2 ceil(ceil(sigma M)/2) (Section 2.1); window
+ * truncation parameter m.
+ *
+ * Layouts.
+ *   x     : N x d row-major float64 (coordinate t of point j at x[j*d + t]).
+ *           Points need not be wrapped; x - floor(x + 1/2) is used.
+ *   f     : N complex samples, interleaved (re, im), in the caller's point order.
+ *   fhat  : M^d complex coefficients in C order over I_M, the entry of k sits at
+ *           sum_t (k_t + M/2) M^(d-1-t) (first coordinate slowest), interleaved.
+ *   Complex values are float2-like (8 bytes) for INFFT_FP32 plans and
+ *   double2-like (16 bytes) for INFFT_FP64 plans.
+ *
+ * Ownership.  The caller owns x, f and fhat.  A plan copies what it needs
+ * from x and owns every device buffer it allocates (sorted points, bins,
+ * work lists, tables, weights, B_opt coefficients, scratch grids) until
+ * infft_destroy.
+ *
+ * Pointers.  f / fhat passed to infft_adjoint / infft_forward may be device
+ * pointers or host pointers; host memory is staged through plan-owned device
+ * buffers with cudaMemcpyAsync on the given stream (synchronising at the end
+ * of the call so that a host result is ready on return).  All other array
+ * arguments documented as "device" must be device pointers.
+ *
+ * Streams.  `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ * default stream.  Calls on device buffers are stream ordered and do not
+ * synchronise the host, except where stated (plan creation, infft_weights,
+ * infft_optimize_B and the getters synchronise).
+ *
+ * Errors.  Every call returns an infft_status and never throws or aborts.
+ * infft_last_error() returns a thread-local message for the last failing call.
+ * A plan stays valid after a failed call unless the status is INFFT_ESTATE.
+ */
+#ifndef INFFT_H
+#define INFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct infft_plan_s* infft_plan_t;
+typedef struct infft_batch_s* infft_batch_t;
+
+typedef enum {
+    INFFT_OK = 0,
+    INFFT_EINVAL = 1,        /* invalid argument (sizes, null pointers, flags) */
+    INFFT_ENOMEM = 2,        /* device or pinned-host allocation failed */
+    INFFT_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    INFFT_ENOTCONV = 4,      /* CG reached max_iter before rel_tol */
+    INFFT_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+    INFFT_ESTATE = 6,        /* call not valid in the plan's state (e.g. DCF before weights) */
+    INFFT_EUNSUPPORTED = 7   /* valid but unsupported size (M_sigma not a power of two, ...) */
+} infft_status;
+
+/* plan flags */
+enum {
+    INFFT_FP32 = 1,          /* spreading / FFT / interpolation in float32 */
+    INFFT_FP64 = 2,          /* everything in float64 */
+    INFFT_WIN_KB = 0,        /* Kaiser-Bessel window (default) */
+    INFFT_WIN_BSPLINE = 4,   /* B-spline window B_{2m}(M_sigma x), eq. window_bspline */
+    INFFT_WIN_DIRICHLET = 8  /* asymmetric Dirichlet window (B_opt only, Theorem 4.5) */
+};
+
+/* reconstruction modes of infft_adjoint */
+enum {
+    INFFT_MODE_PLAIN = 0,    /* h = D^* F^* B^* f          (Algorithm 2.4)            */
+    INFFT_MODE_DCF = 1,      /* h = D^* F^* B^* W f        (Algorithm 3.7)            */
+    INFFT_MODE_BOPT = 2      /* h = D^* F^* B_opt^* f      (Algorithm 4.4)            */
+};
+
+/* options of infft_optimize_B */
+enum {
+    INFFT_BOPT_PATTERN_2M2 = 0,   /* 2m+2 consecutive indices per coordinate (default)       */
+    INFFT_BOPT_PATTERN_PAPER = 1, /* the index set I_{Msigma,m}(x_j) of eq. indexset_x         */
+    INFFT_BOPT_REAL = 2           /* real-constrained least squares instead of complex b_l     */
+};
+
+/*
+ * infft_plan -- create a plan for fixed points (Sections 2-4).
+ *   d      : 1, 2 or 3.
+ *   M      : even degree, M >= 2.
+ *   N      : number of points, 1 <= N < 2^31.
+ *   x      : N x d float64, host or device; copied.
+ *   sigma  : oversampling factor >= 1; M_sigma = 2 ceil(ceil(sigma M)/2) must be a
+ *            power of two <= 4096 (else INFFT_EUNSUPPORTED).
+ *   m      : truncation parameter, 1 <= m, 2m+2 <= M_sigma.
+ *   flags  : INFFT_FP32 or INFFT_FP64, or-ed with a window flag.
+ *   stream : stream for the set-up kernels (the call synchronises it).
+ *   out    : receives the plan.
+ * Sorts the points into tiles of the oversampled grid (counting sort over
+ * grid cells, deterministic order), builds the work lists and the tables of
+ * 1/(M_sigma w^(k)) (eq. matrix_D) and FFT twiddles.
+ */
+infft_status infft_plan(int d, int M, int64_t N, const double* x, double sigma, int m,
+                        unsigned flags, void* stream, infft_plan_t* out);
+
+/*
+ * infft_weights -- Algorithm 3.6: density compensation weights for exact
+ * reconstruction (Corollary 3.4, eq. claim_quadrature_coefficients_double).
+ * If (2M)^d <= N: CG on A_2M^* A_2M u = e_0 (the normal equations of the
+ * second kind, eq. normal_equations_second_kind_double, after conjugation),
+ * w = conj(A_2M u).  Otherwise: CG on A_2M A_2M^* q = 1_N (first kind,
+ * eq. normal_equations_first_kind_double), w = conj(q).  Matrix products are
+ * float64 NFFTs (Algorithms 2.1 / 2.4) at degree 2M with oversampling 2 and
+ * truncation m_cg (<= 0 selects 8 for d <= 2 and 4 for d = 3); CG vectors,
+ * inner products and updates are float64.  x0 = 0, stop when
+ * ||r||_2 / ||b||_2 <= rel_tol or after max_iter iterations.
+ *   residual_inf : (out, may be NULL) max_k |[A_2M^T w]_k - delta_{0,k}| over
+ *                  I_2M, evaluated with the same float64 NFFT.
+ *   iters        : (out, may be NULL) CG iterations taken.
+ * Returns INFFT_ENOTCONV (weights still stored) if max_iter was reached.
+ * Synchronises.
+ */
+infft_status infft_weights(infft_plan_t plan, int max_iter, double rel_tol, int m_cg,
+                           double* residual_inf, int* iters, void* stream);
+
+/* infft_set_weights / infft_get_weights -- N complex128 weights in the caller's
+ * point order (host or device).  set marks the plan ready for INFFT_MODE_DCF. */
+infft_status infft_set_weights(infft_plan_t plan, const void* w, void* stream);
+infft_status infft_get_weights(infft_plan_t plan, void* w, void* stream);
+
+/*
+ * infft_optimize_B -- Algorithm 4.3: for every column l of the sparse matrix B
+ * solve the least-squares problem eq. opt_overdet_columnwise through its
+ * normal equations G_l b_l = v_l, with G_l = H_l^* H_l from the Dirichlet
+ * closed form (eq. matrix_normal_equations_overdet) and v_l from
+ * eq. right_side_normal_equations_overdet, in float64 (one batched kernel,
+ * Cholesky with a diagonal-shift retry).  The window used for w^ is the
+ * plan's window flag (KB, B-spline or Dirichlet).  opts: INFFT_BOPT_* flags.
+ *   max_col_residual : (out, may be NULL) max_l ||H_l b_l - rhs_l||_2^2
+ *                      (eq. res_opt_columnwise), from ||rhs||^2 - Re(b^* v).
+ * Synchronises.
+ */
+infft_status infft_optimize_B(infft_plan_t plan, unsigned opts, double* max_col_residual, void* stream);
+
+/* infft_get_bopt -- copy B_opt coefficients, N x S^d complex128 (S = 2m+2, slot
+ * s_t holds column floor(M_sigma x_t) - m + s_t), caller's point order. */
+infft_status infft_get_bopt(infft_plan_t plan, void* coeff, void* stream);
+
+/*
+ * infft_adjoint -- the reconstruction step.
+ *   mode = INFFT_MODE_PLAIN: Algorithm 2.4, h ~ A^* f;
+ *   mode = INFFT_MODE_DCF  : Algorithm 3.7, h ~ A^* W f (needs weights);
+ *   mode = INFFT_MODE_BOPT : Algorithm 4.4, h = D^* F^* B_opt^* f (needs B_opt).
+ *   f    : N complex samples (host or device), caller's point order.
+ *   fhat : M^d complex result (host or device), C order over I_M.
+ */
+infft_status infft_adjoint(infft_plan_t plan, int mode, const void* f, void* fhat, void* stream);
+
+/* infft_forward -- Algorithm 2.1, f ~ A fhat (fhat: M^d complex, f: N complex). */
+infft_status infft_forward(infft_plan_t plan, const void* fhat, void* f, void* stream);
+
+/*
+ * infft_adjoint_batched -- `count` reconstructions on (possibly different) plans
+ * of the same d and precision, executed as one launch per kernel stage over
+ * all of them.  f[i], fhat[i] are device pointers, or host pointers staged through
+ * the plan's own I/O buffers (then a plan may appear only once in the batch and the
+ * call synchronises).
+ */
+infft_status infft_adjoint_batched(const infft_plan_t* plans, int count, int mode,
+                                   const void* const* f, void* const* fhat, void* stream);
+
+/*
+ * infft_adjoint_batched_timed -- as infft_adjoint_batched (count <= 96), and
+ * reports device times of the stages in stage_ms[5]: spreading, halo merge and
+ * the FFT passes along each axis (unused entries 0), from CUDA events recorded on
+ * `stream` between the kernel launches.  Synchronises.
+ */
+infft_status infft_adjoint_batched_timed(const infft_plan_t* plans, int count, int mode,
+                                         const void* const* f, void* const* fhat, void* stream,
+                                         float* stage_ms);
+
+/*
+ * Graph-replayed batches.  infft_batch_create records the batched adjoint for
+ * fixed plans and fixed device buffers f[i] / fhat[i] into a CUDA graph;
+ * infft_batch_run replays it on `stream`.  The plans and buffers must outlive
+ * the batch.
+ */
+infft_status infft_batch_create(const infft_plan_t* plans, int count, int mode,
+                                const void* const* f, void* const* fhat, void* stream,
+                                infft_batch_t* out);
+infft_status infft_batch_run(infft_batch_t batch, void* stream);
+void infft_batch_destroy(infft_batch_t batch);
+
+/* Accessors. */
+int64_t infft_plan_N(infft_plan_t plan);
+int infft_plan_Msigma(infft_plan_t plan);
+size_t infft_plan_device_bytes(infft_plan_t plan);   /* device memory held by the plan */
+const char* infft_last_error(void);
+void infft_destroy(infft_plan_t plan);
+
+/* Number of kernel launches issued by this thread since the last reset
+ * (for reporting; not synchronised with the device). */
+uint64_t infft_launch_count(void);
+void infft_launch_count_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* INFFT_H */

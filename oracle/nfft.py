@@ -50,7 +50,10 @@ def point_slots(x: np.ndarray, Ms: int, m: int, pattern: str = PATTERN_PAPER):
     s = np.arange(slot_count(m))
     cand = base[:, :, None] - m + s[None, None, :]
     if pattern == PATTERN_PAPER:
-        valid = np.abs(Ms * xw[:, :, None] - cand) <= m
+        # |Ms x - c| <= m decided by comparing Ms x with the integers c - m and c + m,
+        # so that rounding in a subtraction cannot move a tap across the support edge
+        y = (Ms * xw)[:, :, None]
+        valid = (y >= cand - m) & (y <= cand + m)
     elif pattern == PATTERN_2M2:
         valid = np.ones(cand.shape, dtype=bool)
     else:

@@ -1,0 +1,298 @@
+"""ctypes binding of libinfft.so (include/infft.h).
+
+Argument marshalling only: every step of every transform runs in the CUDA
+library.  The raw functions keep the C names (``infft_plan``, ``infft_adjoint``,
+...) and take integer pointers; ``Plan`` and ``Batch`` wrap them for torch
+tensors (device buffers) and numpy arrays (host buffers, staged by the library).
+If the library is missing this module raises instead of falling back to
+anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libinfft.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ETIMEOUT, ESTATE, EUNSUPPORTED = range(8)
+FP32, FP64 = 1, 2
+WIN_KB, WIN_BSPLINE, WIN_DIRICHLET = 0, 4, 8
+MODE_PLAIN, MODE_DCF, MODE_BOPT = 0, 1, 2
+BOPT_PATTERN_2M2, BOPT_PATTERN_PAPER, BOPT_REAL = 0, 1, 2
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTCONV", "ETIMEOUT", "ESTATE", "EUNSUPPORTED"]
+
+
+class InfftError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+_SIGS = {
+    "infft_plan": (C.c_int, [C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_double, C.c_int, C.c_uint, C.c_void_p,
+                             C.POINTER(C.c_void_p)]),
+    "infft_weights": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
+                                C.POINTER(C.c_int), C.c_void_p]),
+    "infft_set_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "infft_get_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "infft_optimize_B": (C.c_int, [C.c_void_p, C.c_uint, C.POINTER(C.c_double), C.c_void_p]),
+    "infft_get_bopt": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "infft_adjoint": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "infft_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "infft_adjoint_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p),
+                                        C.POINTER(C.c_void_p), C.c_void_p]),
+    "infft_adjoint_batched_timed": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p),
+                                              C.POINTER(C.c_void_p), C.c_void_p, C.POINTER(C.c_float)]),
+    "infft_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p),
+                                     C.POINTER(C.c_void_p), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "infft_batch_run": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "infft_batch_destroy": (None, [C.c_void_p]),
+    "infft_plan_N": (C.c_int64, [C.c_void_p]),
+    "infft_plan_Msigma": (C.c_int, [C.c_void_p]),
+    "infft_plan_device_bytes": (C.c_size_t, [C.c_void_p]),
+    "infft_last_error": (C.c_char_p, []),
+    "infft_destroy": (None, [C.c_void_p]),
+    "infft_launch_count": (C.c_uint64, []),
+    "infft_launch_count_reset": (None, []),
+}
+
+EXPORTED = tuple(_SIGS)
+
+
+def load(path: str = LIB_PATH):
+    """Load libinfft.so (built by ``paper_2302_00414_gb300.build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2302_00414_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != OK:
+        raise InfftError(status, load().infft_last_error().decode(errors="replace"))
+
+
+def last_error() -> str:
+    return load().infft_last_error().decode(errors="replace")
+
+
+def launch_count() -> int:
+    return int(load().infft_launch_count())
+
+
+def launch_count_reset():
+    load().infft_launch_count_reset()
+
+
+# ---- raw entry points, same names as the C ABI (integer pointers) ----------------------
+
+def infft_plan(d, M, N, x_ptr, sigma, m, flags, stream=0):
+    out = C.c_void_p()
+    return load().infft_plan(d, M, N, x_ptr, sigma, m, flags, stream, C.byref(out)), out.value
+
+
+def infft_weights(plan, max_iter, rel_tol, m_cg=0, stream=0):
+    res = C.c_double(float("nan"))
+    it = C.c_int(0)
+    s = load().infft_weights(plan, max_iter, rel_tol, m_cg, C.byref(res), C.byref(it), stream)
+    return s, res.value, it.value
+
+
+def infft_optimize_B(plan, opts=0, stream=0):
+    res = C.c_double(float("nan"))
+    s = load().infft_optimize_B(plan, opts, C.byref(res), stream)
+    return s, res.value
+
+
+def infft_adjoint(plan, mode, f_ptr, fhat_ptr, stream=0):
+    return load().infft_adjoint(plan, mode, f_ptr, fhat_ptr, stream)
+
+
+def infft_forward(plan, fhat_ptr, f_ptr, stream=0):
+    return load().infft_forward(plan, fhat_ptr, f_ptr, stream)
+
+
+def infft_adjoint_batched(plans, mode, f_ptrs, fhat_ptrs, stream=0):
+    n = len(plans)
+    P = (C.c_void_p * n)(*plans)
+    F = (C.c_void_p * n)(*f_ptrs)
+    H = (C.c_void_p * n)(*fhat_ptrs)
+    return load().infft_adjoint_batched(P, n, mode, F, H, stream)
+
+
+def infft_destroy(plan):
+    load().infft_destroy(plan)
+
+
+# ---- convenience wrappers ---------------------------------------------------------------
+
+def _ptr(a):
+    """Pointer of a torch tensor (device or host) or a numpy array (host), C-contiguous."""
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if not a.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return a.data_ptr()
+
+
+def _stream(stream):
+    if stream is not None:
+        return int(stream)
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return 0
+
+
+class Plan:
+    """A plan for fixed points x (N x d, float64 numpy array or torch tensor)."""
+
+    def __init__(self, x, M: int, sigma: float = 2.0, m: int = 4, precision: str = "fp32",
+                 window: str = "kb", stream=None):
+        self.precision = precision
+        flags = {"fp32": FP32, "fp64": FP64}[precision]
+        flags |= {"kb": WIN_KB, "bspline": WIN_BSPLINE, "dirichlet": WIN_DIRICHLET}[window]
+        if isinstance(x, np.ndarray):
+            x = np.ascontiguousarray(x, dtype=np.float64)
+            if x.ndim == 1:
+                x = x[:, None]
+            N, d = x.shape
+        else:
+            if x.dtype != __import__("torch").float64:
+                raise ValueError("x must be float64")
+            x = x.contiguous()
+            if x.dim() == 1:
+                x = x[:, None]
+            N, d = x.shape
+        self.d, self.M, self.N, self.m, self.sigma = int(d), int(M), int(N), int(m), float(sigma)
+        s, h = infft_plan(self.d, self.M, self.N, _ptr(x), self.sigma, self.m, flags, _stream(stream))
+        _check(s)
+        self.handle = h
+        self.Ms = int(load().infft_plan_Msigma(h))
+
+    @property
+    def complex_dtype(self):
+        return np.complex64 if self.precision == "fp32" else np.complex128
+
+    @property
+    def device_bytes(self) -> int:
+        return int(load().infft_plan_device_bytes(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            infft_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def weights(self, max_iter: int = 1000, rel_tol: float = 1e-13, m_cg: int = 0, stream=None, check=True):
+        s, res, it = infft_weights(self.handle, max_iter, rel_tol, m_cg, _stream(stream))
+        if check and s not in (OK, ENOTCONV):
+            _check(s)
+        return {"status": s, "residual_inf": res, "iters": it}
+
+    def set_weights(self, w, stream=None):
+        _check(load().infft_set_weights(self.handle, _ptr(w), _stream(stream)))
+
+    def get_weights(self, stream=None) -> np.ndarray:
+        w = np.empty(self.N, dtype=np.complex128)
+        _check(load().infft_get_weights(self.handle, w.ctypes.data, _stream(stream)))
+        return w
+
+    def optimize_B(self, opts: int = 0, stream=None):
+        s, res = infft_optimize_B(self.handle, opts, _stream(stream))
+        _check(s)
+        return res
+
+    def get_bopt(self, stream=None) -> np.ndarray:
+        S = 2 * self.m + 2
+        c = np.empty((self.N,) + (S,) * self.d, dtype=np.complex128)
+        _check(load().infft_get_bopt(self.handle, c.ctypes.data, _stream(stream)))
+        return c
+
+    def adjoint(self, f, fhat=None, mode: int = MODE_PLAIN, stream=None):
+        """fhat = D^* F^* B^* (W) f; f and fhat are torch tensors (device) or numpy arrays (host)."""
+        if fhat is None:
+            if isinstance(f, np.ndarray):
+                fhat = np.empty((self.M,) * self.d, dtype=self.complex_dtype)
+            else:
+                import torch
+                fhat = torch.empty((self.M,) * self.d, dtype=f.dtype, device=f.device)
+        _check(infft_adjoint(self.handle, mode, _ptr(f), _ptr(fhat), _stream(stream)))
+        return fhat
+
+    def forward(self, fhat, f=None, stream=None):
+        if f is None:
+            if isinstance(fhat, np.ndarray):
+                f = np.empty(self.N, dtype=self.complex_dtype)
+            else:
+                import torch
+                f = torch.empty(self.N, dtype=fhat.dtype, device=fhat.device)
+        _check(infft_forward(self.handle, _ptr(fhat), _ptr(f), _stream(stream)))
+        return f
+
+
+def adjoint_batched(plans, fs, fhats, mode: int = MODE_PLAIN, stream=None):
+    _check(infft_adjoint_batched([p.handle for p in plans], mode, [_ptr(f) for f in fs],
+                                 [_ptr(h) for h in fhats], _stream(stream)))
+
+
+def adjoint_batched_timed(plans, fs, fhats, mode: int = MODE_PLAIN, stream=None):
+    """Batched adjoint; returns device times (ms) of spread, merge and the FFT passes."""
+    n = len(plans)
+    P = (C.c_void_p * n)(*[p.handle for p in plans])
+    F = (C.c_void_p * n)(*[_ptr(f) for f in fs])
+    H = (C.c_void_p * n)(*[_ptr(h) for h in fhats])
+    ms = (C.c_float * 5)()
+    _check(load().infft_adjoint_batched_timed(P, n, mode, F, H, _stream(stream), ms))
+    return {"spread": ms[0], "merge": ms[1], "fft": [ms[2 + t] for t in range(plans[0].d)]}
+
+
+class Batch:
+    """A CUDA graph of the batched adjoint over fixed plans and fixed device buffers."""
+
+    def __init__(self, plans, fs, fhats, mode: int = MODE_PLAIN, stream=None):
+        n = len(plans)
+        self._keep = (plans, fs, fhats)
+        P = (C.c_void_p * n)(*[p.handle for p in plans])
+        F = (C.c_void_p * n)(*[_ptr(f) for f in fs])
+        H = (C.c_void_p * n)(*[_ptr(h) for h in fhats])
+        out = C.c_void_p()
+        _check(load().infft_batch_create(P, n, mode, F, H, _stream(stream), C.byref(out)))
+        self.handle = out.value
+
+    def run(self, stream=None):
+        _check(load().infft_batch_run(self.handle, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().infft_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

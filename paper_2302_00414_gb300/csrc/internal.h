@@ -1,0 +1,116 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+struct infft_plan_s {
+    int d, M, Ms, m;
+    int64_t N;
+    double sigma;
+    unsigned flags;
+    bool fp64;
+    int window;               // infft::WindowKind
+    int T, ntile, P, nitems, S;
+    int logMs;
+    double beta;
+
+    // sorted points (device)
+    int* perm = nullptr;
+    uint32_t* cell = nullptr;
+    void* u = nullptr;        // float or double, N*d
+    double* x64 = nullptr;    // wrapped points in sorted order, N*d (B_opt, weights residual)
+    int4* items = nullptr;
+    int* tile_items = nullptr;
+    int* cell_start = nullptr;  // key range + 1 prefix (tile-major cell order)
+    size_t nkeys = 0;
+
+    // tables (device)
+    void* dinv = nullptr;     // M entries
+    void* tw = nullptr;       // Ms/2 complex
+    void* dinv_win = nullptr; // M entries for the B_opt window (may alias dinv)
+
+    // weights (device): caller order float64 master + sorted copy in plan precision
+    void* w_master = nullptr; // N complex128, caller order
+    void* w_sorted = nullptr; // N complex (plan precision), sorted
+    bool has_weights = false;
+
+    // B_opt (device)
+    void* coef = nullptr;     // N*S^d complex (plan precision), sorted
+    double* coef64 = nullptr; // N*S^d complex128, sorted
+    bool has_bopt = false;
+    int bopt_window = 0;
+
+    // scratch (device)
+    void* padded = nullptr;
+    void* grid = nullptr;
+    void* tmp1 = nullptr;
+    void* tmp2 = nullptr;
+    void* io_in = nullptr;    // staging for host inputs / outputs
+    void* io_out = nullptr;
+
+    size_t device_bytes = 0;
+};
+
+struct infft_batch_s {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    void* jobs_dev = nullptr;
+    int* prefix_dev = nullptr;
+};
+
+namespace infft {
+
+// thread-local error message and launch counter
+void set_error(const char* fmt, ...);
+void count_launch(int n = 1);
+
+#define INFFT_CUDA(call)                                                                   \
+    do {                                                                                   \
+        cudaError_t e__ = (call);                                                          \
+        if (e__ != cudaSuccess) {                                                          \
+            infft::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e__),     \
+                             __FILE__, __LINE__);                                          \
+            return INFFT_ECUDA;                                                            \
+        }                                                                                  \
+    } while (0)
+
+#define INFFT_LAUNCHED()                                                                   \
+    do {                                                                                   \
+        infft::count_launch();                                                             \
+        cudaError_t e__ = cudaGetLastError();                                              \
+        if (e__ != cudaSuccess) {                                                          \
+            infft::set_error("kernel launch failed: %s (%s:%d)", cudaGetErrorString(e__),  \
+                             __FILE__, __LINE__);                                          \
+            return INFFT_ECUDA;                                                            \
+        }                                                                                  \
+    } while (0)
+
+#define INFFT_TRY(expr)                                                                    \
+    do {                                                                                   \
+        infft_status s__ = (expr);                                                         \
+        if (s__ != INFFT_OK) return s__;                                                   \
+    } while (0)
+
+infft_status dev_alloc(infft_plan_s* p, void** ptr, size_t bytes);
+bool is_device_pointer(const void* ptr);
+
+// Build the Job descriptors of a list of plans for one transform each.
+template <class R>
+Job<R> make_job(const infft_plan_s* p, int mode, const void* in, void* out);
+
+// Execute transforms for jobs of one d and precision: the adjoint (spread -> merge ->
+// FFT passes with crop and deconvolution) or the forward NFFT (FFT passes with
+// padding -> interpolation); batches larger than the parameter block are chunked.
+// With `ev` (5 events) the adjoint of the first chunk records an event before the
+// spread and after the spread, the merge and each FFT pass.
+template <class R>
+infft_status run_jobs(const std::vector<Job<R>>& jobs, cudaStream_t st, bool forward, cudaEvent_t* ev = nullptr);
+
+}  // namespace infft

@@ -1,0 +1,491 @@
+// NFFT kernels: tile-sorted spreading (Algorithm 2.4 step 1, and its modified
+// forms of Algorithm 3.7 / 4.4), halo merge, d-variate FFT passes with pruned
+// output and per-axis deconvolution (Algorithm 2.4 steps 2-3), zero-padded
+// inverse FFT passes (Algorithm 2.1 steps 1-2) and tile-sorted interpolation
+// (Algorithm 2.1 step 3).
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+#include "jobset.cuh"
+
+namespace infft {
+
+// ---------------------------------------------------------------------------------------
+// spreading: one warp per work item (a tile of T^d grid cells and up to a fixed number of
+// its points).  The warp accumulates into a private padded tile of P^d cells in shared
+// memory (P = T + 2m + 1 covers every tap of every point whose base cell lies in the
+// tile), one point at a time with the lanes over the point's taps, so that no two lanes
+// touch the same cell in one step: no atomics, fixed summation order.  The padded tile
+// is then written out for the merge.
+template <class R, int D>
+__global__ void __launch_bounds__(128) k_spread(const __grid_constant__ JobSet<R> js) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gitem = blockIdx.x * js.wpb + warp;
+    if (gitem >= js.pre_items[js.njobs]) return;
+    const int jb = find_job(js.pre_items, js.njobs, gitem);
+    const Job<R>& J = js.job[jb];
+    const int it = gitem - js.pre_items[jb];
+    const int4 item = J.items[it];
+    const int P = J.P, m = J.m, Ms = J.Ms, T = J.T;
+    const int W = 2 * m + 1;
+    const bool bopt = (J.mode == INFFT_MODE_BOPT);
+    const int S = bopt ? J.S : W;           // taps per axis
+    const int cells = ipow(P, D);
+
+    unsigned char* base = smem_raw + (size_t)warp * js.smem_per_warp;
+    cx<R>* pad = reinterpret_cast<cx<R>*>(base);
+    R* psi = reinterpret_cast<R*>(pad + cells);           // [32][D][W]
+    cx<R>* cst = reinterpret_cast<cx<R>*>(psi + 32 * D * W);  // [32]
+    int* ost = reinterpret_cast<int*>(cst + 32);          // [32][D+1]
+
+    for (int e = lane; e < cells; e += 32) pad[e] = mk<R>(0, 0);
+
+    int tt[D];
+    {
+        int rem = item.x;
+        for (int t = D - 1; t >= 0; --t) { tt[t] = rem % J.ntile; rem /= J.ntile; }
+    }
+    int pstride[D];
+    pstride[D - 1] = 1;
+    for (int t = D - 2; t >= 0; --t) pstride[t] = pstride[t + 1] * P;
+    int ntap = ipow(S, D);
+    __syncwarp();
+
+    for (int c0 = 0; c0 < item.z; c0 += 32) {
+        const int np = min(32, item.z - c0);
+        if (lane < np) {
+            const int i = item.y + c0 + lane;
+            const int j = __ldg(J.perm + i);
+            cx<R> fv = J.in[j];
+            if (J.mode == INFFT_MODE_DCF) fv = mul(J.w[i], fv);
+            uint32_t rem = __ldg(J.cell + i);
+            for (int t = D - 1; t >= 0; --t) {
+                int c = (int)(rem % (uint32_t)Ms);
+                rem /= (uint32_t)Ms;
+                ost[lane * (D + 1) + t] = c - tt[t] * T;
+            }
+            ost[lane * (D + 1) + D] = i;
+            cst[lane] = fv;
+            if (!bopt) {
+                for (int t = 0; t < D; ++t) {
+                    const R u = J.u[(size_t)i * D + t];
+                    for (int s = 0; s < W; ++s)
+                        psi[(lane * D + t) * W + s] = tap_weight<R>(J.window, u, s, m, J.inv_m, J.beta);
+                }
+            }
+        }
+        __syncwarp();
+        for (int p = 0; p < np; ++p) {
+            const cx<R> cv = cst[p];
+            int o[D];
+            for (int t = 0; t < D; ++t) o[t] = ost[p * (D + 1) + t];
+            const int i = ost[p * (D + 1) + D];
+            const R* ps = psi + p * D * W;
+            for (int q = lane; q < ntap; q += 32) {
+                int rem = q, idx = 0;
+                R wgt = R(1);
+                for (int t = D - 1; t >= 0; --t) {
+                    const int s = rem % S;
+                    rem /= S;
+                    idx += (o[t] + s) * pstride[t];
+                    if (!bopt) wgt *= ps[t * W + s];
+                }
+                cx<R> add_v;
+                if (bopt) add_v = mulconj(J.coef[(size_t)i * ntap + q], cv);  // conj(b_{j,l}) f_j
+                else add_v = scale(cv, wgt);
+                pad[idx] = add(pad[idx], add_v);
+            }
+            __syncwarp();
+        }
+    }
+    cx<R>* dst = J.padded + (size_t)it * cells;
+    for (int e = lane; e < cells; e += 32) dst[e] = pad[e];
+}
+
+// ---------------------------------------------------------------------------------------
+// merge: grid cell c receives the sum of every padded-tile cell that maps onto it
+// (padded cell o of tile tl along an axis sits at (tl T - m + o) mod Ms).  One thread per
+// grid cell, work items of a tile summed in item order: deterministic.
+template <class R, int D>
+__global__ void __launch_bounds__(256) k_merge(const __grid_constant__ JobSet<R> js) {
+    const int gblk = blockIdx.x;
+    const int jb = find_job(js.pre_merge, js.njobs, gblk);
+    const Job<R>& J = js.job[jb];
+    const int Ms = J.Ms, T = J.T, m = J.m, P = J.P, nt = J.ntile;
+    const long long total = (long long)ipow(Ms, D);
+    const long long cidx = (long long)(gblk - js.pre_merge[jb]) * blockDim.x + threadIdx.x;
+    if (cidx >= total) return;
+    int c[D];
+    {
+        long long rem = cidx;
+        for (int t = D - 1; t >= 0; --t) { c[t] = (int)(rem % Ms); rem /= Ms; }
+    }
+    int cnt[D], tl[D][8], of[D][8];
+    for (int t = 0; t < D; ++t) {
+        cnt[t] = 0;
+        const int own = c[t] / T;
+        const int ncand = nt >= 3 ? 3 : nt;
+        for (int k = 0; k < ncand; ++k) {
+            const int tile = (nt >= 3) ? mod_pos(own - 1 + k, nt) : k;
+            int o = mod_pos(c[t] - tile * T + m, Ms);
+            for (; o < P && cnt[t] < 8; o += Ms) {
+                tl[t][cnt[t]] = tile;
+                of[t][cnt[t]] = o;
+                ++cnt[t];
+            }
+        }
+    }
+    const int cells = ipow(P, D);
+    cx<R> acc = mk<R>(0, 0);
+    int idx[D];
+    for (int t = 0; t < D; ++t) idx[t] = 0;
+    bool any = true;
+    for (int t = 0; t < D; ++t) any = any && cnt[t] > 0;
+    while (any) {
+        int tile_lin = 0, pidx = 0;
+        for (int t = 0; t < D; ++t) {
+            tile_lin = tile_lin * nt + tl[t][idx[t]];
+            pidx = pidx * P + of[t][idx[t]];
+        }
+        const int i0 = __ldg(J.tile_items + tile_lin), i1 = __ldg(J.tile_items + tile_lin + 1);
+        for (int itm = i0; itm < i1; ++itm) acc = add(acc, J.padded[(size_t)itm * cells + pidx]);
+        int t = D - 1;
+        while (t >= 0) {
+            if (++idx[t] < cnt[t]) break;
+            idx[t] = 0;
+            --t;
+        }
+        if (t < 0) break;
+    }
+    J.grid[cidx] = acc;
+}
+
+// ---------------------------------------------------------------------------------------
+// FFT pass along one axis for a batch of lines held in shared memory: radix-2
+// decimation in time after a bit-reversed load.  Adjoint direction (FWD = false):
+// forward DFT (sign -) of length Ms, keep the M outputs k in I_M, multiply by
+// 1/(Ms w^(k)) of this axis.  Forward direction (FWD = true): the M inputs of I_M times
+// 1/(Ms w^(k)) are placed at k mod Ms, the rest is zero, inverse DFT (sign +).
+// A pass sees a tensor (A, n_in, B): lines run along the middle index with stride B.
+template <class R, int D, bool FWD>
+__global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> js, int pass) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<R>* buf = reinterpret_cast<cx<R>*>(smem_raw);
+    const int gblk = blockIdx.x;
+    const int jb = find_job(js.pre_fft[pass], js.njobs, gblk);
+    const Job<R>& J = js.job[jb];
+    const int lb = gblk - js.pre_fft[pass][jb];
+    const int Ms = J.Ms, M = J.M, L = js.L;
+    const int t = FWD ? pass : D - 1 - pass;
+    const long long A = ipow(Ms, t);
+    const long long B = ipow(M, D - 1 - t);
+    const int n = Ms;
+    const int logn = 31 - __clz(n);
+    const long long nlines = A * B;
+    const long long q0 = (long long)lb * L;
+    const bool lanes_b = (B >= L);  // consecutive lines are consecutive b: coalesce along b
+
+    const cx<R>* src;
+    cx<R>* dst;
+    if (!FWD) {
+        src = (pass == 0) ? J.grid : (pass == 1 ? J.tmp1 : J.tmp2);
+        dst = (pass == D - 1) ? J.out : (pass == 0 ? J.tmp1 : J.tmp2);
+    } else {
+        src = (pass == 0) ? J.in : (pass == 1 ? J.tmp1 : J.tmp2);
+        dst = (pass == D - 1) ? J.grid : (pass == 0 ? J.tmp1 : J.tmp2);
+    }
+    const int tid = threadIdx.x, nth = blockDim.x;
+
+    if (!FWD) {
+        for (int e = tid; e < L * n; e += nth) {
+            int l, i;
+            if (lanes_b) { l = e % L; i = e / L; } else { i = e % n; l = e / n; }
+            const long long q = q0 + l;
+            cx<R> v = mk<R>(0, 0);
+            if (q < nlines) {
+                const long long a = q / B, b = q % B;
+                v = src[(a * n + i) * B + b];
+            }
+            buf[l * n + bitrev(i, logn)] = v;
+        }
+    } else {
+        for (int e = tid; e < L * n; e += nth) buf[e] = mk<R>(0, 0);
+        __syncthreads();
+        for (int e = tid; e < L * M; e += nth) {
+            int l, i;
+            if (lanes_b) { l = e % L; i = e / L; } else { i = e % M; l = e / M; }
+            const long long q = q0 + l;
+            if (q < nlines) {
+                const long long a = q / B, b = q % B;
+                const cx<R> v = scale(src[(a * M + i) * B + b], J.dinv[i]);
+                const int bin = mod_pos(i - M / 2, Ms);
+                buf[l * n + bitrev(bin, logn)] = v;
+            }
+        }
+    }
+    __syncthreads();
+
+    const int half_n = n >> 1;
+    for (int len = 2; len <= n; len <<= 1) {
+        const int half = len >> 1;
+        const int tws = n / len;
+        for (int e = tid; e < L * half_n; e += nth) {
+            const int l = e / half_n, jj = e % half_n;
+            const int grp = jj / half, pos = jj % half;
+            const int i1 = l * n + grp * len + pos, i2 = i1 + half;
+            cx<R> w = J.tw[pos * tws];
+            if (FWD) w.im = -w.im;
+            const cx<R> a = buf[i1];
+            const cx<R> b = mul(w, buf[i2]);
+            buf[i1] = add(a, b);
+            buf[i2] = sub(a, b);
+        }
+        __syncthreads();
+    }
+
+    if (!FWD) {
+        for (int e = tid; e < L * M; e += nth) {
+            int l, i;
+            if (lanes_b) { l = e % L; i = e / L; } else { i = e % M; l = e / M; }
+            const long long q = q0 + l;
+            if (q < nlines) {
+                const long long a = q / B, b = q % B;
+                const int bin = mod_pos(i - M / 2, Ms);
+                dst[(a * M + i) * B + b] = scale(buf[l * n + bin], J.dinv[i]);
+            }
+        }
+    } else {
+        for (int e = tid; e < L * n; e += nth) {
+            int l, i;
+            if (lanes_b) { l = e % L; i = e / L; } else { i = e % n; l = e / n; }
+            const long long q = q0 + l;
+            if (q < nlines) {
+                const long long a = q / B, b = q % B;
+                dst[(a * n + i) * B + b] = buf[l * n + i];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// interpolation (Algorithm 2.1 step 3): one warp per work item; the warp copies the
+// padded tile of the grid around its tile into shared memory, then every lane sums the
+// taps of one point and writes f_j in the caller's order.
+template <class R, int D>
+__global__ void __launch_bounds__(128) k_interp(const __grid_constant__ JobSet<R> js) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gitem = blockIdx.x * js.wpb + warp;
+    if (gitem >= js.pre_items[js.njobs]) return;
+    const int jb = find_job(js.pre_items, js.njobs, gitem);
+    const Job<R>& J = js.job[jb];
+    const int4 item = J.items[gitem - js.pre_items[jb]];
+    const int P = J.P, m = J.m, Ms = J.Ms, T = J.T;
+    const int W = 2 * m + 1;
+    const int cells = ipow(P, D);
+    unsigned char* base = smem_raw + (size_t)warp * js.smem_per_warp;
+    cx<R>* pad = reinterpret_cast<cx<R>*>(base);
+    R* psi = reinterpret_cast<R*>(pad + cells);  // [32][D][W]
+
+    int tt[D];
+    {
+        int rem = item.x;
+        for (int t = D - 1; t >= 0; --t) { tt[t] = rem % J.ntile; rem /= J.ntile; }
+    }
+    for (int e = lane; e < cells; e += 32) {
+        int rem = e;
+        long long g = 0;
+        for (int t = 0; t < D; ++t) {
+            const int div = ipow(P, D - 1 - t);
+            const int o = rem / div;
+            rem -= o * div;
+            g = g * Ms + mod_pos(tt[t] * T - m + o, Ms);
+        }
+        pad[e] = J.grid[g];
+    }
+    int pstride[D];
+    pstride[D - 1] = 1;
+    for (int t = D - 2; t >= 0; --t) pstride[t] = pstride[t + 1] * P;
+    const int ntap = ipow(W, D);
+    __syncwarp();
+
+    for (int c0 = 0; c0 < item.z; c0 += 32) {
+        const int np = min(32, item.z - c0);
+        if (lane < np) {
+            const int i = item.y + c0 + lane;
+            uint32_t rem = __ldg(J.cell + i);
+            int o[D];
+            for (int t = D - 1; t >= 0; --t) {
+                const int c = (int)(rem % (uint32_t)Ms);
+                rem /= (uint32_t)Ms;
+                o[t] = c - tt[t] * T;
+            }
+            R* ps = psi + lane * D * W;
+            for (int t = 0; t < D; ++t) {
+                const R u = J.u[(size_t)i * D + t];
+                for (int s = 0; s < W; ++s) ps[t * W + s] = tap_weight<R>(J.window, u, s, m, J.inv_m, J.beta);
+            }
+            cx<R> acc = mk<R>(0, 0);
+            for (int q = 0; q < ntap; ++q) {
+                int r2 = q, idx = 0;
+                R wgt = R(1);
+                for (int t = D - 1; t >= 0; --t) {
+                    const int s = r2 % W;
+                    r2 /= W;
+                    idx += (o[t] + s) * pstride[t];
+                    wgt *= ps[t * W + s];
+                }
+                const cx<R> g = pad[idx];
+                acc.re += wgt * g.re;
+                acc.im += wgt * g.im;
+            }
+            J.out[__ldg(J.perm + i)] = acc;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// host drivers
+
+static int pick_lines(int n, size_t elem) {
+    const size_t budget = 64 * 1024;
+    int L = 1;
+    while (L < 32 && (size_t)(2 * L) * n * elem <= budget) L *= 2;
+    return L;
+}
+
+template <class R>
+static void fill_prefixes(JobSet<R>& js, int D, bool forward) {
+    js.pre_items[0] = 0;
+    js.pre_merge[0] = 0;
+    for (int p = 0; p < 3; ++p) js.pre_fft[p][0] = 0;
+    int maxMs = 0;
+    for (int j = 0; j < js.njobs; ++j) maxMs = std::max(maxMs, js.job[j].Ms);
+    js.L = pick_lines(maxMs, sizeof(cx<R>));
+    for (int j = 0; j < js.njobs; ++j) {
+        const Job<R>& J = js.job[j];
+        js.pre_items[j + 1] = js.pre_items[j] + J.nitems;
+        const long long cells = (long long)ipow(J.Ms, D);
+        js.pre_merge[j + 1] = js.pre_merge[j] + (int)((cells + 255) / 256);
+        for (int p = 0; p < 3; ++p) {
+            int blocks = 0;
+            if (p < D) {
+                const int t = forward ? p : D - 1 - p;
+                const long long lines = (long long)ipow(J.Ms, t) * ipow(J.M, D - 1 - t);
+                blocks = (int)((lines + js.L - 1) / js.L);
+            }
+            js.pre_fft[p][j + 1] = js.pre_fft[p][j] + blocks;
+        }
+    }
+}
+
+template <class R>
+static size_t spread_smem_per_warp(const JobSet<R>& js, int D) {
+    size_t mx = 0;
+    for (int j = 0; j < js.njobs; ++j) {
+        const Job<R>& J = js.job[j];
+        const int W = 2 * J.m + 1;
+        size_t b = (size_t)ipow(J.P, D) * sizeof(cx<R>) + 32 * D * W * sizeof(R) + 32 * sizeof(cx<R>) +
+                   32 * (D + 1) * sizeof(int);
+        b = (b + 15) & ~(size_t)15;
+        mx = std::max(mx, b);
+    }
+    return mx;
+}
+
+template <class R, int D>
+static infft_status launch_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* ev) {
+    fill_prefixes(js, D, false);
+    if (ev) INFFT_CUDA(cudaEventRecord(ev[0], st));
+    const size_t spw = spread_smem_per_warp(js, D);
+    const size_t smem_cap = 200 * 1024;
+    if (spw > smem_cap) {
+        set_error("padded tile needs %zu bytes of shared memory", spw);
+        return INFFT_EUNSUPPORTED;
+    }
+    js.smem_per_warp = (int)spw;
+    js.wpb = (int)std::max<size_t>(1, std::min<size_t>(4, smem_cap / spw));
+    const int nitems = js.pre_items[js.njobs];
+    if (nitems > 0) {
+        const size_t smem = spw * js.wpb;
+        INFFT_CUDA(cudaFuncSetAttribute(k_spread<R, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_spread<R, D><<<(nitems + js.wpb - 1) / js.wpb, 32 * js.wpb, smem, st>>>(js);
+        INFFT_LAUNCHED();
+    }
+    if (ev) INFFT_CUDA(cudaEventRecord(ev[1], st));
+    k_merge<R, D><<<js.pre_merge[js.njobs], 256, 0, st>>>(js);
+    INFFT_LAUNCHED();
+    if (ev) INFFT_CUDA(cudaEventRecord(ev[2], st));
+    int maxMs = 0;
+    for (int j = 0; j < js.njobs; ++j) maxMs = std::max(maxMs, js.job[j].Ms);
+    const size_t fsmem = (size_t)js.L * maxMs * sizeof(cx<R>);
+    INFFT_CUDA(cudaFuncSetAttribute(k_fft<R, D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
+    for (int p = 0; p < D; ++p) {
+        k_fft<R, D, false><<<js.pre_fft[p][js.njobs], 256, fsmem, st>>>(js, p);
+        INFFT_LAUNCHED();
+        if (ev) INFFT_CUDA(cudaEventRecord(ev[3 + p], st));
+    }
+    return INFFT_OK;
+}
+
+template <class R, int D>
+static infft_status launch_forward(JobSet<R>& js, cudaStream_t st) {
+    fill_prefixes(js, D, true);
+    int maxMs = 0;
+    for (int j = 0; j < js.njobs; ++j) maxMs = std::max(maxMs, js.job[j].Ms);
+    const size_t fsmem = (size_t)js.L * maxMs * sizeof(cx<R>);
+    INFFT_CUDA(cudaFuncSetAttribute(k_fft<R, D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
+    for (int p = 0; p < D; ++p) {
+        k_fft<R, D, true><<<js.pre_fft[p][js.njobs], 256, fsmem, st>>>(js, p);
+        INFFT_LAUNCHED();
+    }
+    size_t spw = 0;
+    for (int j = 0; j < js.njobs; ++j) {
+        const Job<R>& J = js.job[j];
+        size_t b = (size_t)ipow(J.P, D) * sizeof(cx<R>) + 32 * D * (2 * J.m + 1) * sizeof(R);
+        spw = std::max(spw, (b + 15) & ~(size_t)15);
+    }
+    const size_t smem_cap = 200 * 1024;
+    if (spw > smem_cap) {
+        set_error("padded tile needs %zu bytes of shared memory", spw);
+        return INFFT_EUNSUPPORTED;
+    }
+    js.smem_per_warp = (int)spw;
+    js.wpb = (int)std::max<size_t>(1, std::min<size_t>(4, smem_cap / spw));
+    const int nitems = js.pre_items[js.njobs];
+    if (nitems > 0) {
+        const size_t smem = spw * js.wpb;
+        INFFT_CUDA(cudaFuncSetAttribute(k_interp<R, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_interp<R, D><<<(nitems + js.wpb - 1) / js.wpb, 32 * js.wpb, smem, st>>>(js);
+        INFFT_LAUNCHED();
+    }
+    return INFFT_OK;
+}
+
+template <class R>
+infft_status run_jobs(const std::vector<Job<R>>& jobs, cudaStream_t st, bool forward, cudaEvent_t* ev) {
+    if (jobs.empty()) return INFFT_OK;
+    const int D = jobs[0].d;
+    for (size_t s = 0; s < jobs.size(); s += MAXJ) {
+        JobSet<R> js;
+        memset(&js, 0, sizeof(js));
+        js.njobs = (int)std::min<size_t>(MAXJ, jobs.size() - s);
+        for (int j = 0; j < js.njobs; ++j) js.job[j] = jobs[s + j];
+        infft_status r;
+        if (!forward) {
+            cudaEvent_t* e = (s == 0) ? ev : nullptr;
+            r = D == 1 ? launch_adjoint<R, 1>(js, st, e) : D == 2 ? launch_adjoint<R, 2>(js, st, e) : launch_adjoint<R, 3>(js, st, e);
+        } else {
+            r = D == 1 ? launch_forward<R, 1>(js, st) : D == 2 ? launch_forward<R, 2>(js, st) : launch_forward<R, 3>(js, st);
+        }
+        if (r != INFFT_OK) return r;
+    }
+    return INFFT_OK;
+}
+
+template infft_status run_jobs<float>(const std::vector<Job<float>>&, cudaStream_t, bool, cudaEvent_t*);
+template infft_status run_jobs<double>(const std::vector<Job<double>>&, cudaStream_t, bool, cudaEvent_t*);
+
+}  // namespace infft

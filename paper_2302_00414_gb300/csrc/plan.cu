@@ -1,0 +1,626 @@
+// Plan creation (point binning, tables) and the C-ABI entry points of the
+// transforms (Algorithms 2.1, 2.4, 3.7, 4.4).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+#include "jobset.cuh"
+
+namespace infft {
+
+
+// ----------------------------------------------------------------------------------------
+// error state and launch counter
+static thread_local char g_err[512] = "";
+static thread_local uint64_t g_launches = 0;
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+void count_launch(int n) { g_launches += (uint64_t)n; }
+
+infft_status dev_alloc(infft_plan_s* p, void** ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (bytes == 0) return INFFT_OK;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        return INFFT_ENOMEM;
+    }
+    if (p) p->device_bytes += bytes;
+    return INFFT_OK;
+}
+
+bool is_device_pointer(const void* ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ----------------------------------------------------------------------------------------
+// binning kernels
+
+// Wrap x into [-1/2, 1/2), split M_sigma x into base cell and fractional offset, and
+// compute the tile-major cell key.  The arithmetic mirrors x - floor(x + 1/2),
+// M_sigma * x, floor, with correctly rounded operations and no contraction.
+__global__ void k_prep(const double* __restrict__ x, int N, int d, int Ms, int T, int nt,
+                       uint32_t* __restrict__ key, uint32_t* __restrict__ cellrm,
+                       double* __restrict__ u, double* __restrict__ xw_out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    uint32_t tile = 0, intile = 0, rm = 0;
+    for (int t = 0; t < d; ++t) {
+        const double xv = x[(size_t)j * d + t];
+        const double xw = __dsub_rn(xv, floor(__dadd_rn(xv, 0.5)));
+        const double y = __dmul_rn((double)Ms, xw);
+        const double bf = floor(y);
+        u[(size_t)j * d + t] = __dsub_rn(y, bf);
+        xw_out[(size_t)j * d + t] = xw;
+        int c = (int)bf % Ms;
+        if (c < 0) c += Ms;
+        tile = tile * nt + c / T;
+        intile = intile * T + c % T;
+        rm = rm * Ms + c;
+    }
+    uint32_t tpow = 1;
+    for (int t = 0; t < d; ++t) tpow *= T;
+    key[j] = tile * tpow + intile;
+    cellrm[j] = rm;
+}
+
+__global__ void k_hist(const uint32_t* __restrict__ key, int N, int* __restrict__ count) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < N) atomicAdd(count + key[j], 1);
+}
+
+// exclusive scan, 1024 elements per block
+__global__ void k_scan_block(int* __restrict__ data, long long n, int* __restrict__ block_sums) {
+    __shared__ int wsum[32];
+    const long long i = (long long)blockIdx.x * 1024 + threadIdx.x;
+    int v = (i < n) ? data[i] : 0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int s = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        wsum[lane] = s;  // inclusive scan of warp sums
+    }
+    __syncthreads();
+    const int before = (wid > 0) ? wsum[wid - 1] : 0;
+    if (i < n) data[i] = before + incl - v;
+    if (threadIdx.x == 1023 && block_sums) block_sums[blockIdx.x] = wsum[31];
+}
+
+__global__ void k_scan_add(int* __restrict__ data, long long n, const int* __restrict__ block_off) {
+    const long long i = (long long)blockIdx.x * 1024 + threadIdx.x;
+    if (i < n) data[i] += block_off[blockIdx.x];
+}
+
+static infft_status scan_exclusive(int* data, long long n, cudaStream_t st) {
+    const long long nb = (n + 1023) / 1024;
+    if (nb == 1) {
+        k_scan_block<<<1, 1024, 0, st>>>(data, n, nullptr);
+        INFFT_LAUNCHED();
+        return INFFT_OK;
+    }
+    int* sums = nullptr;
+    INFFT_CUDA(cudaMallocAsync((void**)&sums, nb * sizeof(int), st));
+    k_scan_block<<<(unsigned)nb, 1024, 0, st>>>(data, n, sums);
+    INFFT_LAUNCHED();
+    infft_status s = scan_exclusive(sums, nb, st);
+    if (s != INFFT_OK) { cudaFreeAsync(sums, st); return s; }
+    k_scan_add<<<(unsigned)nb, 1024, 0, st>>>(data, n, sums);
+    INFFT_LAUNCHED();
+    INFFT_CUDA(cudaFreeAsync(sums, st));
+    return INFFT_OK;
+}
+
+__global__ void k_scatter(const uint32_t* __restrict__ key, int N, const int* __restrict__ start,
+                          int* __restrict__ fill, int* __restrict__ order) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const uint32_t k = key[j];
+    order[start[k] + atomicAdd(fill + k, 1)] = j;
+}
+
+// points of one cell in ascending caller index: makes the order (and therefore every
+// floating-point summation order downstream) independent of the scatter's atomics.
+__global__ void k_cell_sort(const int* __restrict__ start, long long nkeys, int* __restrict__ order) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nkeys) return;
+    const int a = start[k], b = start[k + 1];
+    for (int i = a + 1; i < b; ++i) {
+        const int v = order[i];
+        int p = i - 1;
+        while (p >= a && order[p] > v) { order[p + 1] = order[p]; --p; }
+        order[p + 1] = v;
+    }
+}
+
+template <class R>
+__global__ void k_gather(const int* __restrict__ order, int N, int d, const uint32_t* __restrict__ cellrm,
+                         const double* __restrict__ u, const double* __restrict__ xw, uint32_t* __restrict__ cell_s,
+                         R* __restrict__ u_s, double* __restrict__ x_s) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int j = order[i];
+    cell_s[i] = cellrm[j];
+    for (int t = 0; t < d; ++t) {
+        u_s[(size_t)i * d + t] = (R)u[(size_t)j * d + t];
+        x_s[(size_t)i * d + t] = xw[(size_t)j * d + t];
+    }
+}
+
+// 1/(M_sigma w^(k)) for k in I_M (one axis of eq. matrix_D) and FFT twiddles exp(-2 pi i k/Ms).
+template <class R>
+__global__ void k_tables(int M, int Ms, int m, int window, double beta, R* __restrict__ dinv,
+                         cx<R>* __restrict__ tw, double* __restrict__ dinv64) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M) {
+        const double k = (double)(i - M / 2);
+        double wh;
+        if (window == WK_KB) {
+            const double a = 2.0 * M_PI * m * k / Ms;
+            const double r = beta * beta - a * a;
+            double q;
+            if (r > 0) { const double s = sqrt(r); q = sinh(s) / s; }
+            else if (r < 0) { const double s = sqrt(-r); q = sin(s) / s; }
+            else q = 1.0;
+            wh = (2.0 * m / Ms) * q;
+        } else if (window == WK_BSPLINE) {
+            const double t = k / Ms;
+            const double s = (k == 0) ? 1.0 : sinpi(t) / (M_PI * t);
+            wh = pow(s, 2 * m) / Ms;
+        } else {
+            wh = 1.0;
+        }
+        const double v = 1.0 / (Ms * wh);
+        dinv[i] = (R)v;
+        if (dinv64) dinv64[i] = v;
+    }
+    if (i < Ms / 2) {
+        double s, c;
+        sincospi(2.0 * i / Ms, &s, &c);
+        tw[i] = mk<R>((R)c, (R)(-s));
+    }
+}
+
+// ----------------------------------------------------------------------------------------
+template <class R>
+Job<R> make_job(const infft_plan_s* p, int mode, const void* in, void* out) {
+    Job<R> J;
+    memset(&J, 0, sizeof(J));
+    J.d = p->d; J.M = p->M; J.Ms = p->Ms; J.m = p->m;
+    J.N = (int)p->N; J.T = p->T; J.ntile = p->ntile; J.P = p->P;
+    J.nitems = p->nitems; J.window = p->window; J.mode = mode; J.S = p->S;
+    J.beta = (R)p->beta; J.inv_m = (R)(1.0 / p->m);
+    J.perm = p->perm; J.cell = p->cell; J.u = (const R*)p->u;
+    J.w = (const cx<R>*)p->w_sorted; J.coef = (const cx<R>*)p->coef;
+    J.items = p->items; J.tile_items = p->tile_items;
+    J.dinv = (mode == INFFT_MODE_BOPT && p->dinv_win) ? (const R*)p->dinv_win : (const R*)p->dinv;
+    J.tw = (const cx<R>*)p->tw;
+    J.padded = (cx<R>*)p->padded; J.grid = (cx<R>*)p->grid;
+    J.tmp1 = (cx<R>*)p->tmp1; J.tmp2 = (cx<R>*)p->tmp2;
+    J.in = (const cx<R>*)in; J.out = (cx<R>*)out;
+    return J;
+}
+template Job<float> make_job<float>(const infft_plan_s*, int, const void*, void*);
+template Job<double> make_job<double>(const infft_plan_s*, int, const void*, void*);
+
+static void free_plan(infft_plan_s* p) {
+    if (!p) return;
+    void* ptrs[] = {p->perm, p->cell, p->u, p->x64, p->items, p->tile_items, p->cell_start, p->dinv, p->tw,
+                    p->dinv_win, p->w_master, p->w_sorted, p->coef, p->coef64, p->padded, p->grid, p->tmp1,
+                    p->tmp2, p->io_in, p->io_out};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    delete p;
+}
+
+static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+static infft_status build_plan(infft_plan_s* p, const double* x_in, cudaStream_t st) {
+    const int d = p->d, Ms = p->Ms, m = p->m;
+    const int N = (int)p->N;
+    const size_t R_sz = p->fp64 ? sizeof(double) : sizeof(float);
+    const size_t C_sz = 2 * R_sz;
+
+    // tiles: T^d cells, T > m
+    const int Tdef = d == 1 ? 256 : (d == 2 ? 16 : 8);
+    p->T = std::min(Tdef, Ms);
+    if (p->T <= m) {
+        set_error("tile edge %d must exceed m = %d", p->T, m);
+        return INFFT_EUNSUPPORTED;
+    }
+    p->ntile = (Ms + p->T - 1) / p->T;
+    p->P = p->T + 2 * m + 1;
+    p->S = 2 * m + 2;
+    long long nkeys = 1;
+    for (int t = 0; t < d; ++t) nkeys *= (long long)p->ntile * p->T;
+    p->nkeys = (size_t)nkeys;
+    long long msd = 1;
+    for (int t = 0; t < d; ++t) msd *= Ms;
+    if (nkeys >= (1ll << 31) || msd >= (1ll << 31)) {
+        set_error("grid too large");
+        return INFFT_EUNSUPPORTED;
+    }
+
+    // points to the device
+    double* x_dev = nullptr;
+    const bool x_on_dev = is_device_pointer(x_in);
+    INFFT_CUDA(cudaMalloc((void**)&x_dev, (size_t)N * d * sizeof(double)));
+    INFFT_CUDA(cudaMemcpyAsync(x_dev, x_in, (size_t)N * d * sizeof(double),
+                               x_on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    uint32_t *key = nullptr, *cellrm = nullptr;
+    double *u64 = nullptr, *xw = nullptr;
+    int *count = nullptr, *fill = nullptr, *order = nullptr;
+    INFFT_CUDA(cudaMalloc((void**)&key, (size_t)N * 4));
+    INFFT_CUDA(cudaMalloc((void**)&cellrm, (size_t)N * 4));
+    INFFT_CUDA(cudaMalloc((void**)&u64, (size_t)N * d * 8));
+    INFFT_CUDA(cudaMalloc((void**)&xw, (size_t)N * d * 8));
+    INFFT_CUDA(cudaMalloc((void**)&fill, (size_t)(nkeys + 1) * 4));
+    INFFT_CUDA(cudaMalloc((void**)&order, (size_t)N * 4));
+    INFFT_TRY(dev_alloc(p, (void**)&p->cell_start, (size_t)(nkeys + 1) * 4));
+    count = p->cell_start;
+    INFFT_CUDA(cudaMemsetAsync(count, 0, (size_t)(nkeys + 1) * 4, st));
+    INFFT_CUDA(cudaMemsetAsync(fill, 0, (size_t)(nkeys + 1) * 4, st));
+
+    const int tb = 256;
+    const int gb = (N + tb - 1) / tb;
+    k_prep<<<gb, tb, 0, st>>>(x_dev, N, d, Ms, p->T, p->ntile, key, cellrm, u64, xw);
+    INFFT_LAUNCHED();
+    k_hist<<<gb, tb, 0, st>>>(key, N, count);
+    INFFT_LAUNCHED();
+    INFFT_TRY(scan_exclusive(count, nkeys + 1, st));
+    k_scatter<<<gb, tb, 0, st>>>(key, N, count, fill, order);
+    INFFT_LAUNCHED();
+    k_cell_sort<<<(unsigned)((nkeys + 255) / 256), 256, 0, st>>>(count, nkeys, order);
+    INFFT_LAUNCHED();
+
+    INFFT_TRY(dev_alloc(p, (void**)&p->perm, (size_t)N * 4));
+    INFFT_TRY(dev_alloc(p, (void**)&p->cell, (size_t)N * 4));
+    INFFT_TRY(dev_alloc(p, &p->u, (size_t)N * d * R_sz));
+    INFFT_TRY(dev_alloc(p, (void**)&p->x64, (size_t)N * d * 8));
+    INFFT_CUDA(cudaMemcpyAsync(p->perm, order, (size_t)N * 4, cudaMemcpyDeviceToDevice, st));
+    if (p->fp64)
+        k_gather<double><<<gb, tb, 0, st>>>(order, N, d, cellrm, u64, xw, p->cell, (double*)p->u, p->x64);
+    else
+        k_gather<float><<<gb, tb, 0, st>>>(order, N, d, cellrm, u64, xw, p->cell, (float*)p->u, p->x64);
+    INFFT_LAUNCHED();
+
+    // work items: split each tile's points into chunks of at most `cap`
+    long long tpow = 1, ntl = 1;
+    for (int t = 0; t < d; ++t) { tpow *= p->T; ntl *= p->ntile; }
+    const int ntiles = (int)ntl;  // nkeys = ntiles * tpow
+    std::vector<int> cs(nkeys + 1);
+    INFFT_CUDA(cudaMemcpyAsync(cs.data(), count, (size_t)(nkeys + 1) * 4, cudaMemcpyDeviceToHost, st));
+    INFFT_CUDA(cudaStreamSynchronize(st));
+    const int cap = d == 3 ? 128 : 512;
+    std::vector<int4> items;
+    std::vector<int> tile_items(ntiles + 1, 0);
+    for (int tl = 0; tl < ntiles; ++tl) {
+        tile_items[tl] = (int)items.size();
+        const int a = cs[(size_t)tl * tpow], b = cs[(size_t)(tl + 1) * tpow];
+        for (int s = a; s < b; s += cap) items.push_back(make_int4(tl, s, std::min(cap, b - s), 0));
+    }
+    tile_items[ntiles] = (int)items.size();
+    p->nitems = (int)items.size();
+    INFFT_TRY(dev_alloc(p, (void**)&p->items, std::max<size_t>(1, items.size()) * sizeof(int4)));
+    INFFT_TRY(dev_alloc(p, (void**)&p->tile_items, (size_t)(ntiles + 1) * 4));
+    if (!items.empty())
+        INFFT_CUDA(cudaMemcpy(p->items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    INFFT_CUDA(cudaMemcpy(p->tile_items, tile_items.data(), (size_t)(ntiles + 1) * 4, cudaMemcpyHostToDevice));
+
+    cudaFree(x_dev); cudaFree(key); cudaFree(cellrm); cudaFree(u64); cudaFree(xw); cudaFree(fill); cudaFree(order);
+
+    // tables
+    INFFT_TRY(dev_alloc(p, &p->dinv, (size_t)p->M * R_sz));
+    INFFT_TRY(dev_alloc(p, &p->tw, (size_t)(Ms / 2) * C_sz));
+    const int nt = std::max(p->M, Ms / 2);
+    if (p->fp64)
+        k_tables<double><<<(nt + 255) / 256, 256, 0, st>>>(p->M, Ms, m, p->window, p->beta, (double*)p->dinv,
+                                                          (cx<double>*)p->tw, nullptr);
+    else
+        k_tables<float><<<(nt + 255) / 256, 256, 0, st>>>(p->M, Ms, m, p->window, p->beta, (float*)p->dinv,
+                                                         (cx<float>*)p->tw, nullptr);
+    INFFT_LAUNCHED();
+
+    // scratch
+    long long pd = 1, msd_ = 1;
+    for (int t = 0; t < d; ++t) { pd *= p->P; msd_ *= Ms; }
+    INFFT_TRY(dev_alloc(p, &p->padded, std::max<size_t>(1, (size_t)p->nitems) * pd * C_sz));
+    INFFT_TRY(dev_alloc(p, &p->grid, (size_t)msd_ * C_sz));
+    size_t t1 = 0, t2 = 0;
+    if (d >= 2) t1 = (size_t)ipow(Ms, d - 1) * p->M;
+    if (d == 3) t2 = (size_t)Ms * p->M * p->M;
+    // forward direction uses (M, M, Ms)... sizes: pass0 out Ms*M^(d-1), pass1 out Ms^2*M^(d-2)
+    if (d >= 2) t1 = std::max(t1, (size_t)Ms * (size_t)ipow(p->M, d - 1));
+    if (d == 3) t2 = std::max(t2, (size_t)Ms * Ms * p->M);
+    if (t1) INFFT_TRY(dev_alloc(p, &p->tmp1, t1 * C_sz));
+    if (t2) INFFT_TRY(dev_alloc(p, &p->tmp2, t2 * C_sz));
+    INFFT_CUDA(cudaStreamSynchronize(st));
+    return INFFT_OK;
+}
+
+}  // namespace infft
+
+using namespace infft;
+
+extern "C" {
+
+const char* infft_last_error(void) { return g_err; }
+uint64_t infft_launch_count(void) { return g_launches; }
+void infft_launch_count_reset(void) { g_launches = 0; }
+
+infft_status infft_plan(int d, int M, int64_t N, const double* x, double sigma, int m, unsigned flags, void* stream,
+                        infft_plan_t* out) {
+    if (!out) { set_error("out is NULL"); return INFFT_EINVAL; }
+    *out = nullptr;
+    if (d < 1 || d > 3 || M < 2 || (M & 1) || N < 1 || N >= (1ll << 31) || !x || !(sigma >= 1.0) || m < 1) {
+        set_error("invalid plan arguments (d=%d M=%d N=%lld sigma=%g m=%d)", d, M, (long long)N, sigma, m);
+        return INFFT_EINVAL;
+    }
+    const bool fp64 = (flags & INFFT_FP64) != 0;
+    if (((flags & INFFT_FP32) != 0) == fp64) { set_error("exactly one of INFFT_FP32 / INFFT_FP64"); return INFFT_EINVAL; }
+    const int Ms = 2 * (int)std::ceil(std::ceil(sigma * M) / 2.0);
+    if (2 * m + 2 > Ms) { set_error("2m+2 = %d exceeds M_sigma = %d", 2 * m + 2, Ms); return INFFT_EINVAL; }
+    if (!is_pow2(Ms) || Ms > 4096) { set_error("M_sigma = %d must be a power of two <= 4096", Ms); return INFFT_EUNSUPPORTED; }
+    if (2 * m > 16 && (flags & INFFT_WIN_BSPLINE)) { set_error("B-spline order 2m > 16"); return INFFT_EUNSUPPORTED; }
+    infft_plan_s* p = new infft_plan_s();
+    p->d = d; p->M = M; p->Ms = Ms; p->m = m; p->N = N; p->sigma = sigma; p->flags = flags; p->fp64 = fp64;
+    p->window = (flags & INFFT_WIN_BSPLINE) ? WK_BSPLINE : ((flags & INFFT_WIN_DIRICHLET) ? WK_DIRICHLET : WK_KB);
+    p->beta = M_PI * m * (2.0 - (double)M / Ms);
+    int l = 0;
+    while ((1 << l) < Ms) ++l;
+    p->logMs = l;
+    infft_status s = build_plan(p, x, (cudaStream_t)stream);
+    if (s != INFFT_OK) { free_plan(p); return s; }
+    *out = p;
+    return INFFT_OK;
+}
+
+void infft_destroy(infft_plan_t p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    free_plan(p);
+}
+
+#ifdef INFFT_DEBUG
+// debug builds only: copy an internal buffer of the plan to host memory
+infft_status infft_debug_copy(infft_plan_t p, int which, void* host, size_t bytes) {
+    const void* src[] = {p->padded, p->grid, p->items, p->tile_items, p->perm, p->cell, p->u, p->dinv, p->tw,
+                         p->cell_start, p->tmp1};
+    if (which < 0 || which > 10 || !src[which]) return INFFT_EINVAL;
+    cudaDeviceSynchronize();
+    INFFT_CUDA(cudaMemcpy(host, src[which], bytes, cudaMemcpyDeviceToHost));
+    return INFFT_OK;
+}
+int infft_debug_info(infft_plan_t p, int which) {
+    int v[] = {p->T, p->ntile, p->P, p->nitems, p->S, (int)p->nkeys};
+    return v[which];
+}
+#endif
+
+int64_t infft_plan_N(infft_plan_t p) { return p ? p->N : -1; }
+int infft_plan_Msigma(infft_plan_t p) { return p ? p->Ms : -1; }
+size_t infft_plan_device_bytes(infft_plan_t p) { return p ? p->device_bytes : 0; }
+
+static infft_status check_mode(infft_plan_t p, int mode) {
+    if (mode == INFFT_MODE_DCF && !p->has_weights) { set_error("DCF mode needs weights"); return INFFT_ESTATE; }
+    if (mode == INFFT_MODE_BOPT && !p->has_bopt) { set_error("BOPT mode needs infft_optimize_B"); return INFFT_ESTATE; }
+    if (mode < 0 || mode > 2) { set_error("bad mode %d", mode); return INFFT_EINVAL; }
+    if (mode != INFFT_MODE_BOPT && p->window == WK_DIRICHLET) {
+        set_error("the Dirichlet window only serves B_opt");
+        return INFFT_ESTATE;
+    }
+    return INFFT_OK;
+}
+
+static size_t coeff_count(const infft_plan_s* p) {
+    size_t k = 1;
+    for (int t = 0; t < p->d; ++t) k *= (size_t)p->M;
+    return k;
+}
+
+static infft_status ensure_io(infft_plan_s* p) {
+    const size_t C = p->fp64 ? 16 : 8;
+    if (!p->io_in) INFFT_TRY(dev_alloc(p, &p->io_in, std::max((size_t)p->N, coeff_count(p)) * C));
+    if (!p->io_out) INFFT_TRY(dev_alloc(p, &p->io_out, std::max((size_t)p->N, coeff_count(p)) * C));
+    return INFFT_OK;
+}
+
+static infft_status transform(infft_plan_t p, int mode, const void* in, void* out, void* stream, bool forward) {
+    if (!p || !in || !out) { set_error("null argument"); return INFFT_EINVAL; }
+    if (!forward) INFFT_TRY(check_mode(p, mode));
+    else if (p->window == WK_DIRICHLET) { set_error("no forward NFFT with the Dirichlet window"); return INFFT_ESTATE; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t C = p->fp64 ? 16 : 8;
+    const size_t nin = forward ? coeff_count(p) : (size_t)p->N;
+    const size_t nout = forward ? (size_t)p->N : coeff_count(p);
+    const bool in_dev = is_device_pointer(in), out_dev = is_device_pointer(out);
+    const void* din = in;
+    void* dout = out;
+    if (!in_dev || !out_dev) INFFT_TRY(ensure_io(p));
+    if (!in_dev) {
+        INFFT_CUDA(cudaMemcpyAsync(p->io_in, in, nin * C, cudaMemcpyHostToDevice, st));
+        din = p->io_in;
+    }
+    if (!out_dev) dout = p->io_out;
+    infft_status s;
+    if (p->fp64) {
+        std::vector<Job<double>> jobs{make_job<double>(p, mode, din, dout)};
+        s = run_jobs<double>(jobs, st, forward);
+    } else {
+        std::vector<Job<float>> jobs{make_job<float>(p, mode, din, dout)};
+        s = run_jobs<float>(jobs, st, forward);
+    }
+    if (s != INFFT_OK) return s;
+    if (!out_dev) {
+        INFFT_CUDA(cudaMemcpyAsync(out, dout, nout * C, cudaMemcpyDeviceToHost, st));
+        INFFT_CUDA(cudaStreamSynchronize(st));
+    }
+    return INFFT_OK;
+}
+
+infft_status infft_adjoint(infft_plan_t p, int mode, const void* f, void* fhat, void* stream) {
+    return transform(p, mode, f, fhat, stream, false);
+}
+
+infft_status infft_forward(infft_plan_t p, const void* fhat, void* f, void* stream) {
+    return transform(p, INFFT_MODE_PLAIN, fhat, f, stream, true);
+}
+
+static infft_status batched_jobs_check(const infft_plan_t* plans, int count, int mode) {
+    if (!plans || count < 1) { set_error("empty batch"); return INFFT_EINVAL; }
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i]) { set_error("null plan %d", i); return INFFT_EINVAL; }
+        if (plans[i]->d != plans[0]->d || plans[i]->fp64 != plans[0]->fp64) {
+            set_error("batched plans must share d and precision");
+            return INFFT_EINVAL;
+        }
+        INFFT_TRY(check_mode(plans[i], mode));
+    }
+    return INFFT_OK;
+}
+
+static infft_status run_batched(const infft_plan_t* plans, int count, int mode, const void* const* f,
+                                void* const* fhat, cudaStream_t st, cudaEvent_t* ev = nullptr) {
+    // host buffers are staged through each plan's I/O buffers (a plan may then appear once)
+    std::vector<const void*> fin(count);
+    std::vector<void*> fout(count);
+    bool any_host_out = false;
+    for (int i = 0; i < count; ++i) {
+        infft_plan_s* p = plans[i];
+        const size_t C = p->fp64 ? 16 : 8;
+        fin[i] = f[i];
+        fout[i] = fhat[i];
+        const bool in_dev = is_device_pointer(f[i]), out_dev = is_device_pointer(fhat[i]);
+        if (!in_dev || !out_dev) INFFT_TRY(ensure_io(p));
+        if (!in_dev) {
+            INFFT_CUDA(cudaMemcpyAsync(p->io_in, f[i], (size_t)p->N * C, cudaMemcpyHostToDevice, st));
+            fin[i] = p->io_in;
+        }
+        if (!out_dev) { fout[i] = p->io_out; any_host_out = true; }
+    }
+    infft_status s;
+    if (plans[0]->fp64) {
+        std::vector<Job<double>> jobs;
+        for (int i = 0; i < count; ++i) jobs.push_back(make_job<double>(plans[i], mode, fin[i], fout[i]));
+        s = run_jobs<double>(jobs, st, false, ev);
+    } else {
+        std::vector<Job<float>> jobs;
+        for (int i = 0; i < count; ++i) jobs.push_back(make_job<float>(plans[i], mode, fin[i], fout[i]));
+        s = run_jobs<float>(jobs, st, false, ev);
+    }
+    if (s != INFFT_OK) return s;
+    if (any_host_out) {
+        for (int i = 0; i < count; ++i) {
+            if (fout[i] == fhat[i]) continue;
+            const size_t C = plans[i]->fp64 ? 16 : 8;
+            INFFT_CUDA(cudaMemcpyAsync(fhat[i], fout[i], coeff_count(plans[i]) * C, cudaMemcpyDeviceToHost, st));
+        }
+        INFFT_CUDA(cudaStreamSynchronize(st));
+    }
+    return INFFT_OK;
+}
+
+infft_status infft_adjoint_batched_timed(const infft_plan_t* plans, int count, int mode, const void* const* f,
+                                         void* const* fhat, void* stream, float* stage_ms) {
+    INFFT_TRY(batched_jobs_check(plans, count, mode));
+    if (!f || !fhat || !stage_ms) { set_error("null buffers"); return INFFT_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t ev[6];
+    for (int i = 0; i < 6; ++i) INFFT_CUDA(cudaEventCreate(&ev[i]));
+    infft_status s = run_batched(plans, count, mode, f, fhat, st, ev);
+    if (s == INFFT_OK) {
+        cudaError_t e = cudaEventSynchronize(ev[2 + plans[0]->d]);
+        if (e != cudaSuccess) { set_error("event sync: %s", cudaGetErrorString(e)); s = INFFT_ECUDA; }
+    }
+    if (s == INFFT_OK) {
+        for (int k = 0; k < 5; ++k) stage_ms[k] = 0.f;
+        cudaEventElapsedTime(&stage_ms[0], ev[0], ev[1]);
+        cudaEventElapsedTime(&stage_ms[1], ev[1], ev[2]);
+        for (int p = 0; p < plans[0]->d; ++p) cudaEventElapsedTime(&stage_ms[2 + p], ev[2 + p], ev[3 + p]);
+    }
+    for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
+    return s;
+}
+
+infft_status infft_adjoint_batched(const infft_plan_t* plans, int count, int mode, const void* const* f,
+                                   void* const* fhat, void* stream) {
+    INFFT_TRY(batched_jobs_check(plans, count, mode));
+    if (!f || !fhat) { set_error("null buffers"); return INFFT_EINVAL; }
+    return run_batched(plans, count, mode, f, fhat, (cudaStream_t)stream);
+}
+
+infft_status infft_batch_create(const infft_plan_t* plans, int count, int mode, const void* const* f,
+                                void* const* fhat, void* stream, infft_batch_t* out) {
+    if (!out) { set_error("out is NULL"); return INFFT_EINVAL; }
+    *out = nullptr;
+    INFFT_TRY(batched_jobs_check(plans, count, mode));
+    if (!f || !fhat) { set_error("null buffers"); return INFFT_EINVAL; }
+    cudaStream_t cap;
+    INFFT_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    infft_batch_s* b = new infft_batch_s();
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        set_error("begin capture: %s", cudaGetErrorString(e));
+        delete b;
+        cudaStreamDestroy(cap);
+        return INFFT_ECUDA;
+    }
+    infft_status s = run_batched(plans, count, mode, f, fhat, cap);
+    e = cudaStreamEndCapture(cap, &b->graph);
+    cudaStreamDestroy(cap);
+    if (s != INFFT_OK || e != cudaSuccess) {
+        if (s == INFFT_OK) set_error("end capture: %s", cudaGetErrorString(e));
+        if (b->graph) cudaGraphDestroy(b->graph);
+        delete b;
+        return s != INFFT_OK ? s : INFFT_ECUDA;
+    }
+    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) {
+        set_error("graph instantiate: %s", cudaGetErrorString(e));
+        cudaGraphDestroy(b->graph);
+        delete b;
+        return INFFT_ECUDA;
+    }
+    (void)stream;
+    *out = b;
+    return INFFT_OK;
+}
+
+infft_status infft_batch_run(infft_batch_t b, void* stream) {
+    if (!b) { set_error("null batch"); return INFFT_EINVAL; }
+    INFFT_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    count_launch();
+    return INFFT_OK;
+}
+
+void infft_batch_destroy(infft_batch_t b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    delete b;
+}
+
+}  // extern "C"

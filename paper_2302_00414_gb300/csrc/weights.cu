@@ -1,0 +1,342 @@
+// Density compensation weights (Algorithm 3.6, Corollary 3.4) by CG in float64.
+//
+// With A = A_{2M} (eq. matrix_A at degree 2M):
+//  * |I_2M| <= N: the normal equations of the second kind A^T conj(A) v = e_0,
+//    w = conj(A) v (eq. normal_equations_second_kind_double).  Writing u = conj(v)
+//    they become A^* A u = e_0 and w = conj(A u): CG on the Hermitian operator
+//    A^* A (an NFFT followed by an adjoint NFFT).
+//  * |I_2M| > N: the normal equations of the first kind conj(A) A^T w = 1_N
+//    (eq. normal_equations_first_kind_double).  With q = conj(w) they become
+//    A A^* q = 1_N: CG on A A^* (adjoint NFFT followed by NFFT), w = conj(q).
+// The products are float64 NFFTs of an internal plan at degree 2M (sigma = 2)
+// whose point order is the parent plan's sorted order, so the resulting weights
+// are already in the order the spreading kernels read them.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+#include "jobset.cuh"
+
+namespace infft {
+
+
+constexpr int RED_BLOCKS = 1024;
+constexpr int RED_THREADS = 256;
+
+// partial sums of sum_i conj(a_i) b_i over a fixed grid: deterministic
+__global__ void __launch_bounds__(RED_THREADS) k_dot_partial(const cx<double>* __restrict__ a,
+                                                             const cx<double>* __restrict__ b, long long n,
+                                                             double* __restrict__ part) {
+    __shared__ double sre[RED_THREADS], sim[RED_THREADS];
+    double re = 0, im = 0;
+    for (long long i = (long long)blockIdx.x * RED_THREADS + threadIdx.x; i < n; i += (long long)RED_BLOCKS * RED_THREADS) {
+        const cx<double> x = a[i], y = b[i];
+        re += x.re * y.re + x.im * y.im;
+        im += x.re * y.im - x.im * y.re;
+    }
+    sre[threadIdx.x] = re;
+    sim[threadIdx.x] = im;
+    __syncthreads();
+    for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sre[threadIdx.x] += sre[threadIdx.x + s];
+            sim[threadIdx.x] += sim[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = sre[0];
+        part[2 * blockIdx.x + 1] = sim[0];
+    }
+}
+
+// out[0..1] = sum of the partials (fixed order)
+__global__ void k_dot_final(const double* __restrict__ part, double* __restrict__ out) {
+    __shared__ double sre[RED_THREADS], sim[RED_THREADS];
+    double re = 0, im = 0;
+    for (int i = threadIdx.x; i < RED_BLOCKS; i += RED_THREADS) { re += part[2 * i]; im += part[2 * i + 1]; }
+    sre[threadIdx.x] = re;
+    sim[threadIdx.x] = im;
+    __syncthreads();
+    for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) { sre[threadIdx.x] += sre[threadIdx.x + s]; sim[threadIdx.x] += sim[threadIdx.x + s]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { out[0] = sre[0]; out[1] = sim[0]; }
+}
+
+// CG scalars: s[0] = rr, s[2] = <p, q>, s[4] = rr_new, s[6] = alpha, s[7] = beta
+__global__ void k_cg_alpha(double* s) { s[6] = (s[2] != 0.0) ? s[0] / s[2] : 0.0; }
+__global__ void k_cg_beta(double* s) {
+    s[7] = (s[0] != 0.0) ? s[4] / s[0] : 0.0;
+    s[0] = s[4];
+}
+
+__global__ void k_cg_update_xr(cx<double>* __restrict__ x, cx<double>* __restrict__ r, const cx<double>* __restrict__ p,
+                               const cx<double>* __restrict__ q, long long n, const double* __restrict__ s) {
+    const double al = s[6];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        x[i] = add(x[i], scale(p[i], al));
+        r[i] = sub(r[i], scale(q[i], al));
+    }
+}
+
+__global__ void k_cg_update_p(cx<double>* __restrict__ p, const cx<double>* __restrict__ r, long long n,
+                              const double* __restrict__ s) {
+    const double be = s[7];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = add(r[i], scale(p[i], be));
+}
+
+__global__ void k_conj(const cx<double>* __restrict__ a, cx<double>* __restrict__ b, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = conjg(a[i]);
+}
+
+__global__ void k_fill(cx<double>* __restrict__ a, long long n, cx<double> v) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+
+// max_k |conj(r_k) - delta_{0,k}|, partial maxima per block
+__global__ void __launch_bounds__(RED_THREADS) k_resid_partial(const cx<double>* __restrict__ r, long long n,
+                                                               long long k0, double* __restrict__ part) {
+    __shared__ double sm[RED_THREADS];
+    double mx = 0;
+    for (long long i = (long long)blockIdx.x * RED_THREADS + threadIdx.x; i < n; i += (long long)RED_BLOCKS * RED_THREADS) {
+        double re = r[i].re, im = -r[i].im;
+        if (i == k0) re -= 1.0;
+        mx = fmax(mx, sqrt(re * re + im * im));
+    }
+    sm[threadIdx.x] = mx;
+    __syncthreads();
+    for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+__global__ void k_max_final(const double* __restrict__ part, double* __restrict__ out) {
+    __shared__ double sm[RED_THREADS];
+    double mx = 0;
+    for (int i = threadIdx.x; i < RED_BLOCKS; i += RED_THREADS) mx = fmax(mx, part[i]);
+    sm[threadIdx.x] = mx;
+    __syncthreads();
+    for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sm[0];
+}
+
+// weights in sorted order -> caller order (complex128) and plan-precision sorted copy
+template <class R>
+__global__ void k_store_weights(const cx<double>* __restrict__ ws, const int* __restrict__ perm, int N,
+                                cx<double>* __restrict__ master, cx<R>* __restrict__ sorted) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const cx<double> v = ws[i];
+    master[perm[i]] = v;
+    sorted[i] = mk<R>((R)v.re, (R)v.im);
+}
+
+template <class R>
+__global__ void k_sort_weights(const cx<double>* __restrict__ master, const int* __restrict__ perm, int N,
+                               cx<R>* __restrict__ sorted) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const cx<double> v = master[perm[i]];
+    sorted[i] = mk<R>((R)v.re, (R)v.im);
+}
+
+static infft_status nfft64(infft_plan_s* q, bool forward, const void* in, void* out, cudaStream_t st) {
+    std::vector<Job<double>> jobs{make_job<double>(q, INFFT_MODE_PLAIN, in, out)};
+    return run_jobs<double>(jobs, st, forward);
+}
+
+static infft_status dot(const cx<double>* a, const cx<double>* b, long long n, double* part, double* out,
+                        cudaStream_t st) {
+    k_dot_partial<<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, b, n, part);
+    INFFT_LAUNCHED();
+    k_dot_final<<<1, RED_THREADS, 0, st>>>(part, out);
+    INFFT_LAUNCHED();
+    return INFFT_OK;
+}
+
+static infft_status ensure_weight_buffers(infft_plan_s* p) {
+    const size_t R_sz = p->fp64 ? 8 : 4;
+    if (!p->w_master) INFFT_TRY(dev_alloc(p, &p->w_master, (size_t)p->N * 16));
+    if (!p->w_sorted) INFFT_TRY(dev_alloc(p, &p->w_sorted, (size_t)p->N * 2 * R_sz));
+    return INFFT_OK;
+}
+
+static infft_status weights_impl(infft_plan_s* p, int max_iter, double rel_tol, int m_cg, double* residual_inf,
+                                 int* iters_out, cudaStream_t st, std::vector<void*>& tmp, infft_plan_t& sub) {
+    const int d = p->d, M2 = 2 * p->M;
+    const int N = (int)p->N;
+    if (m_cg <= 0) m_cg = (d <= 2) ? 8 : 4;
+    const int Ms2 = 2 * M2;
+    m_cg = std::min(m_cg, (Ms2 - 2) / 2);
+    INFFT_TRY(infft_plan(d, M2, N, p->x64, 2.0, m_cg, INFFT_FP64 | INFFT_WIN_KB, st, &sub));
+    long long K = 1;
+    for (int t = 0; t < d; ++t) K *= M2;
+    const bool second_kind = K <= N;
+    const long long n = second_kind ? K : N;   // CG unknowns
+    const long long aux_n = second_kind ? N : K;
+    auto alloc = [&](size_t bytes) -> void* {
+        void* q = nullptr;
+        if (cudaMalloc(&q, bytes) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+        tmp.push_back(q);
+        return q;
+    };
+    cx<double>* x = (cx<double>*)alloc(n * 16);
+    cx<double>* r = (cx<double>*)alloc(n * 16);
+    cx<double>* pv = (cx<double>*)alloc(n * 16);
+    cx<double>* qv = (cx<double>*)alloc(n * 16);
+    cx<double>* aux = (cx<double>*)alloc(std::max(aux_n, (long long)N) * 16);
+    cx<double>* ws = (cx<double>*)alloc((size_t)N * 16);
+    cx<double>* kv = (cx<double>*)alloc(K * 16);
+    double* part = (double*)alloc(2 * RED_BLOCKS * 8);
+    double* sc = (double*)alloc(16 * 8);
+    double* bn = (double*)alloc(16);
+    if (!x || !r || !pv || !qv || !aux || !ws || !kv || !part || !sc || !bn) {
+        set_error("CG buffers: out of device memory");
+        return INFFT_ENOMEM;
+    }
+    const int eb = 1024, et = 256;
+    // x = 0; r = b; p = b
+    INFFT_CUDA(cudaMemsetAsync(x, 0, n * 16, st));
+    if (second_kind) {
+        INFFT_CUDA(cudaMemsetAsync(r, 0, n * 16, st));
+        long long k0 = 0;
+        for (int t = 0; t < d; ++t) k0 = k0 * M2 + M2 / 2;
+        k_fill<<<1, 1, 0, st>>>(r + k0, 1, mk<double>(1.0, 0.0));
+        INFFT_LAUNCHED();
+    } else {
+        k_fill<<<eb, et, 0, st>>>(r, n, mk<double>(1.0, 0.0));
+        INFFT_LAUNCHED();
+    }
+    INFFT_CUDA(cudaMemcpyAsync(pv, r, n * 16, cudaMemcpyDeviceToDevice, st));
+    INFFT_TRY(dot(r, r, n, part, sc + 0, st));  // rr
+    INFFT_CUDA(cudaMemcpyAsync(bn, sc + 0, 8, cudaMemcpyDeviceToDevice, st));
+    double b2 = 0;
+    INFFT_CUDA(cudaMemcpyAsync(&b2, bn, 8, cudaMemcpyDeviceToHost, st));
+    INFFT_CUDA(cudaStreamSynchronize(st));
+    const double bnorm = std::sqrt(b2);
+
+    int it = 0;
+    bool conv = false;
+    for (it = 0; it < max_iter; ++it) {
+        // q = op(p)
+        if (second_kind) {
+            INFFT_TRY(nfft64(sub, true, pv, aux, st));    // A p   (K -> N)
+            INFFT_TRY(nfft64(sub, false, aux, qv, st));   // A^* (A p)
+        } else {
+            INFFT_TRY(nfft64(sub, false, pv, aux, st));   // A^* p (N -> K)
+            INFFT_TRY(nfft64(sub, true, aux, qv, st));    // A (A^* p)
+        }
+        INFFT_TRY(dot(pv, qv, n, part, sc + 2, st));
+        k_cg_alpha<<<1, 1, 0, st>>>(sc);
+        INFFT_LAUNCHED();
+        k_cg_update_xr<<<eb, et, 0, st>>>(x, r, pv, qv, n, sc);
+        INFFT_LAUNCHED();
+        INFFT_TRY(dot(r, r, n, part, sc + 4, st));
+        double rr_new = 0;
+        INFFT_CUDA(cudaMemcpyAsync(&rr_new, sc + 4, 8, cudaMemcpyDeviceToHost, st));
+        k_cg_beta<<<1, 1, 0, st>>>(sc);
+        INFFT_LAUNCHED();
+        k_cg_update_p<<<eb, et, 0, st>>>(pv, r, n, sc);
+        INFFT_LAUNCHED();
+        INFFT_CUDA(cudaStreamSynchronize(st));
+        if (!(rr_new == rr_new)) { set_error("CG breakdown (NaN)"); return INFFT_ENOTCONV; }
+        if (std::sqrt(rr_new) <= rel_tol * bnorm) { ++it; conv = true; break; }
+    }
+    // weights in sorted order
+    if (second_kind) {
+        INFFT_TRY(nfft64(sub, true, x, aux, st));  // A u
+        k_conj<<<eb, et, 0, st>>>(aux, ws, N);
+    } else {
+        k_conj<<<eb, et, 0, st>>>(x, ws, N);
+    }
+    INFFT_LAUNCHED();
+    INFFT_TRY(ensure_weight_buffers(p));
+    if (p->fp64)
+        k_store_weights<double><<<(N + 255) / 256, 256, 0, st>>>(ws, p->perm, N, (cx<double>*)p->w_master,
+                                                                 (cx<double>*)p->w_sorted);
+    else
+        k_store_weights<float><<<(N + 255) / 256, 256, 0, st>>>(ws, p->perm, N, (cx<double>*)p->w_master,
+                                                                (cx<float>*)p->w_sorted);
+    INFFT_LAUNCHED();
+    p->has_weights = true;
+    if (residual_inf) {
+        // A^T w = conj(A^* conj(w)) on I_2M
+        k_conj<<<eb, et, 0, st>>>(ws, aux, N);
+        INFFT_LAUNCHED();
+        INFFT_TRY(nfft64(sub, false, aux, kv, st));
+        long long k0 = 0;
+        for (int t = 0; t < d; ++t) k0 = k0 * M2 + M2 / 2;
+        k_resid_partial<<<RED_BLOCKS, RED_THREADS, 0, st>>>(kv, K, k0, part);
+        INFFT_LAUNCHED();
+        k_max_final<<<1, RED_THREADS, 0, st>>>(part, sc + 8);
+        INFFT_LAUNCHED();
+        INFFT_CUDA(cudaMemcpyAsync(residual_inf, sc + 8, 8, cudaMemcpyDeviceToHost, st));
+    }
+    INFFT_CUDA(cudaStreamSynchronize(st));
+    if (iters_out) *iters_out = it;
+    if (!conv) {
+        set_error("CG did not reach rel_tol %g in %d iterations", rel_tol, max_iter);
+        return INFFT_ENOTCONV;
+    }
+    return INFFT_OK;
+}
+
+}  // namespace infft
+
+using namespace infft;
+
+extern "C" {
+
+infft_status infft_weights(infft_plan_t p, int max_iter, double rel_tol, int m_cg, double* residual_inf, int* iters,
+                           void* stream) {
+    if (!p || max_iter < 1 || !(rel_tol >= 0)) { set_error("invalid weights arguments"); return INFFT_EINVAL; }
+    std::vector<void*> tmp;
+    infft_plan_t sub = nullptr;
+    infft_status s = weights_impl(p, max_iter, rel_tol, m_cg, residual_inf, iters, (cudaStream_t)stream, tmp, sub);
+    cudaStreamSynchronize((cudaStream_t)stream);
+    for (void* q : tmp) cudaFree(q);
+    if (sub) infft_destroy(sub);
+    return s;
+}
+
+infft_status infft_set_weights(infft_plan_t p, const void* w, void* stream) {
+    if (!p || !w) { set_error("null argument"); return INFFT_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    INFFT_TRY(ensure_weight_buffers(p));
+    const bool dev = is_device_pointer(w);
+    INFFT_CUDA(cudaMemcpyAsync(p->w_master, w, (size_t)p->N * 16, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    const int N = (int)p->N;
+    if (p->fp64)
+        k_sort_weights<double><<<(N + 255) / 256, 256, 0, st>>>((const cx<double>*)p->w_master, p->perm, N,
+                                                                (cx<double>*)p->w_sorted);
+    else
+        k_sort_weights<float><<<(N + 255) / 256, 256, 0, st>>>((const cx<double>*)p->w_master, p->perm, N,
+                                                               (cx<float>*)p->w_sorted);
+    INFFT_LAUNCHED();
+    INFFT_CUDA(cudaStreamSynchronize(st));
+    p->has_weights = true;
+    return INFFT_OK;
+}
+
+infft_status infft_get_weights(infft_plan_t p, void* w, void* stream) {
+    if (!p || !w) { set_error("null argument"); return INFFT_EINVAL; }
+    if (!p->has_weights) { set_error("no weights"); return INFFT_ESTATE; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool dev = is_device_pointer(w);
+    INFFT_CUDA(cudaMemcpyAsync(w, p->w_master, (size_t)p->N * 16, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    INFFT_CUDA(cudaStreamSynchronize(st));
+    return INFFT_OK;
+}
+
+}  // extern "C"

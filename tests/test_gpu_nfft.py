@@ -1,0 +1,164 @@
+"""Parity of the CUDA adjoint NFFT / NFFT (Algorithms 2.4 / 2.1) with the FP64 oracle.
+
+FP64 plans run the same algorithm as the oracle's Algorithm 2.4 / 2.1, so they
+are compared with it at 1e-12.  FP32 plans are compared with the exact sums
+(eq. nfft*, eq. nfft) at the 1e-5 relative l2 bound required for FP32
+spreading, and with the oracle's Algorithm 2.4 at a bound derived from float32
+rounding (1e-5 as well).  Sizes span several tiles and ragged tails.
+"""
+import numpy as np
+import pytest
+
+import inputs
+from oracle import fourier as FO
+from oracle import nfft as NF
+from tests.gpu_util import lib_or_skip, rel, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def kb_bound(m, sigma):
+    """Kaiser-Bessel error estimate of the cited window literature (see test_oracle_nfft)."""
+    s = np.sqrt(1 - 1 / sigma)
+    return 4 * np.pi * (np.sqrt(m) + m) * s ** 0.5 * np.exp(-2 * np.pi * m * s)
+
+CASES = [  # d, M, N, sigma, m, generator
+    (1, 64, 256, 2.0, 6, "jitter"),
+    (1, 128, 1001, 2.0, 4, "random"),
+    (2, 32, 3000, 2.0, 4, "random"),
+    (2, 64, 9001, 2.0, 6, "random"),
+    (2, 16, 200, 2.0, 2, "random"),
+    (2, 64, 4096, 2.0, 4, "polar"),
+    (2, 8, 50, 2.0, 3, "random"),
+    (3, 16, 2000, 2.0, 3, "random"),
+    (3, 8, 700, 2.0, 2, "random"),
+]
+
+
+def points(d, N, gen, seed):
+    if gen == "jitter":
+        return inputs.jittered_1d(N, seed)
+    if gen == "polar":
+        n = int(np.sqrt(N))
+        return inputs.polar(n, n)
+    return inputs.random_points(N, d, seed)
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"d{c[0]}M{c[1]}N{c[2]}m{c[4]}{c[5]}" for c in CASES])
+def test_adjoint_fp64_matches_oracle_algorithm(case):
+    L, torch = lib_or_skip()
+    d, M, N, sigma, m, gen = case
+    x = points(d, N, gen, 1)
+    N = x.shape[0]
+    f = inputs.samples_complex(N, 2)
+    ref = NF.adjoint_nfft(x, f, M, sigma, m)
+    p = L.Plan(x, M, sigma, m, "fp64")
+    h = p.adjoint(to_dev(torch, f)).cpu().numpy().ravel()
+    assert rel(h, ref) < 1e-12
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"d{c[0]}M{c[1]}N{c[2]}m{c[4]}{c[5]}" for c in CASES])
+def test_forward_fp64_matches_oracle_algorithm(case):
+    L, torch = lib_or_skip()
+    d, M, N, sigma, m, gen = case
+    x = points(d, N, gen, 3)
+    fh = inputs.coeffs_complex((M,) * d, 4)
+    ref = NF.nfft(x, fh, M, sigma, m)
+    p = L.Plan(x, M, sigma, m, "fp64")
+    f = p.forward(to_dev(torch, fh)).cpu().numpy()
+    assert rel(f, ref) < 1e-12
+
+
+@pytest.mark.parametrize("d,M,N,m", [(1, 64, 256, 6), (2, 64, 9001, 6), (2, 64, 9001, 4), (2, 128, 20000, 4),
+                                     (3, 16, 3000, 4)])
+def test_fp32_within_1e5_of_exact_sums(d, M, N, m):
+    L, torch = lib_or_skip()
+    x = inputs.random_points(N, d, 5)
+    f = inputs.samples_complex(N, 6)
+    p = L.Plan(x, M, 2.0, m, "fp32")
+    h = p.adjoint(to_dev(torch, f, torch.complex64)).cpu().numpy()
+    assert rel(h, FO.adjoint_ndft(x, f, M)) < 1e-5
+    fh = inputs.coeffs_complex((M,) * d, 7)
+    fx = p.forward(to_dev(torch, fh, torch.complex64)).cpu().numpy()
+    assert rel(fx, FO.ndft(x, fh, M)) < 1e-5
+
+
+def test_edge_points_and_single_point():
+    L, torch = lib_or_skip()
+    M, sigma, m = 16, 2.0, 4
+    # points on the boundary of the torus, below -1/2, on grid nodes, duplicates
+    x = np.array([[-0.5, -0.5], [0.5 - 1e-12, 0.25], [-0.5 - 1e-3, 0.0], [0.0, 0.0], [0.0, 0.0],
+                  [1.0 / 32, -3.0 / 32], [0.49999, -0.49999]])
+    f = inputs.samples_complex(len(x), 8)
+    p = L.Plan(x, M, sigma, m, "fp64")
+    h = p.adjoint(to_dev(torch, f)).cpu().numpy()
+    assert rel(h, NF.adjoint_nfft(x, f, M, sigma, m)) < 1e-12
+    # N = 1
+    x1 = np.array([[0.3141, -0.2718]])
+    p1 = L.Plan(x1, M, sigma, m, "fp64")
+    h1 = p1.adjoint(to_dev(torch, np.array([1.0 + 0j]))).cpu().numpy().ravel()
+    K = FO.index_set(M, 2)
+    assert np.max(np.abs(h1 - np.exp(-2j * np.pi * (K @ x1[0])))) < kb_bound(m, sigma)
+
+
+def test_host_buffers_equal_device_buffers():
+    L, torch = lib_or_skip()
+    x = inputs.random_points(5000, 2, 9)
+    f = inputs.samples_complex(5000, 10).astype(np.complex64)
+    p = L.Plan(x, 64, 2.0, 4, "fp32")
+    hd = p.adjoint(to_dev(torch, f)).cpu().numpy()
+    hh = p.adjoint(f)  # numpy in, numpy out: staged by the library
+    assert np.array_equal(hd, hh)
+
+
+def test_deterministic_bitwise():
+    L, torch = lib_or_skip()
+    x = inputs.polar(128, 64)
+    f = to_dev(torch, inputs.samples_complex(x.shape[0], 11), torch.complex64)
+    p = L.Plan(x, 64, 2.0, 4, "fp32")
+    a = p.adjoint(f).cpu().numpy()
+    b = p.adjoint(f).cpu().numpy()
+    q = L.Plan(x, 64, 2.0, 4, "fp32")
+    c = q.adjoint(f).cpu().numpy()
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
+def test_batched_and_graph_equal_single_calls():
+    L, torch = lib_or_skip()
+    sets = inputs.batch_sets(6, 12, Ms=(16, 32, 64))
+    plans, fs, outs, singles = [], [], [], []
+    for i, (M, x) in enumerate(sets):
+        p = L.Plan(x, M, 2.0, 4, "fp32")
+        f = to_dev(torch, inputs.samples_complex(x.shape[0], 100 + i), torch.complex64)
+        plans.append(p)
+        fs.append(f)
+        outs.append(torch.empty((M, M), dtype=torch.complex64, device="cuda"))
+        singles.append(p.adjoint(f).cpu().numpy())
+    L.adjoint_batched(plans, fs, outs)
+    for o, s in zip(outs, singles):
+        assert np.array_equal(o.cpu().numpy(), s)
+    g_outs = [torch.zeros_like(o) for o in outs]
+    b = L.Batch(plans, fs, g_outs)
+    b.run()
+    torch.cuda.synchronize()
+    for o, s in zip(g_outs, singles):
+        assert np.array_equal(o.cpu().numpy(), s)
+
+
+def test_error_codes():
+    L, torch = lib_or_skip()
+    x = inputs.random_points(100, 2, 13)
+    with pytest.raises(L.InfftError) as e:
+        L.Plan(x, 15, 2.0, 4)
+    assert e.value.status == 1  # EINVAL: M odd
+    with pytest.raises(L.InfftError) as e:
+        L.Plan(x, 12, 2.0, 4)
+    assert e.value.status == 7  # EUNSUPPORTED: M_sigma = 24
+    with pytest.raises(L.InfftError) as e:
+        L.Plan(x, 4, 2.0, 4)
+    assert e.value.status == 1  # 2m+2 > M_sigma
+    p = L.Plan(x, 16, 2.0, 4)
+    f = to_dev(torch, inputs.samples_complex(100, 1), torch.complex64)
+    with pytest.raises(L.InfftError) as e:
+        p.adjoint(f, mode=L.MODE_DCF)
+    assert e.value.status == 6  # ESTATE: no weights yet

@@ -1,0 +1,93 @@
+"""Parity of the CUDA weight solve (Algorithm 3.6) and the density-compensated
+reconstruction (Algorithm 3.7) with the FP64 oracle."""
+import numpy as np
+import pytest
+
+import inputs
+from oracle import fourier as FO
+from oracle import weights as WT
+from tests.gpu_util import lib_or_skip, rel, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def kb_bound(m, sigma):
+    s = np.sqrt(1 - 1 / sigma)
+    return 4 * np.pi * (np.sqrt(m) + m) * s ** 0.5 * np.exp(-2 * np.pi * m * s)
+
+
+def test_c1_weights_and_exact_reconstruction_fp64():
+    """d=1, M=64, N=256 jittered points, sigma=2, m=6, FP64 (the one-dimensional workload)."""
+    L, torch = lib_or_skip()
+    x = inputs.jittered_1d(256, 0)
+    M = 64
+    p = L.Plan(x, M, 2.0, 6, "fp64")
+    info = p.weights(max_iter=500, rel_tol=1e-14)
+    w = p.get_weights()
+    w_ref = WT.weights(x, M)
+    assert rel(w, w_ref) < 1e-10
+    assert info["residual_inf"] < 1e-12
+    assert WT.residual_inf(x, w, M) < 1e-12
+    fh = inputs.coeffs_complex((M,), 0)
+    f = FO.ndft(x, fh, M)
+    h = p.adjoint(to_dev(torch, f), mode=L.MODE_DCF).cpu().numpy()
+    assert rel(h, fh) < 1e-10          # exact reconstruction (Corollary 3.4), to NFFT accuracy
+    assert rel(h, WT.reconstruct_exact(x, f, w, M)) < kb_bound(6, 2.0)
+
+
+def test_equispaced_weights_one_over_N():
+    L, torch = lib_or_skip()
+    x = inputs.equispaced(32, 2)
+    p = L.Plan(x, 8, 2.0, 4, "fp64")
+    p.weights(max_iter=200, rel_tol=1e-14)
+    w = p.get_weights()
+    assert np.max(np.abs(w - 1.0 / x.shape[0])) < 1e-12
+
+
+@pytest.mark.parametrize("d,M,N", [(2, 8, 600), (2, 16, 1500)])
+def test_second_kind_weights_match_dense_solution(d, M, N):
+    L, torch = lib_or_skip()
+    x = inputs.random_points(N, d, 21)
+    p = L.Plan(x, M, 2.0, 6, "fp64")
+    info = p.weights(max_iter=2000, rel_tol=1e-13)
+    w = p.get_weights()
+    w_ref = WT.weights(x, M)
+    assert rel(w, w_ref) < 1e-8
+    eps = WT.residual_inf(x, w, M)
+    assert eps < 1e-10 and info["residual_inf"] == pytest.approx(eps, rel=0.5, abs=1e-12)
+    fh = inputs.coeffs_complex((M,) * d, 22)
+    f = FO.ndft(x, fh, M)
+    # Theorem 3.14(i) on the exact sums with the GPU weights ...
+    assert rel(WT.reconstruct_exact(x, f, w, M), fh) <= M ** d * eps + 1e-13
+    # ... and the GPU reconstruction adds at most the NFFT approximation error
+    h = p.adjoint(to_dev(torch, f), mode=L.MODE_DCF).cpu().numpy()
+    assert rel(h, fh) <= M ** d * eps + kb_bound(6, 2.0)
+
+
+def test_first_kind_weights_least_squares():
+    L, torch = lib_or_skip()
+    x = inputs.random_points(50, 1, 31)
+    M = 64  # |I_2M| = 128 > N = 50
+    p = L.Plan(x, M, 2.0, 6, "fp64")
+    p.weights(max_iter=3000, rel_tol=1e-12)
+    w = p.get_weights()
+    A = FO.matrix_A(x, 2 * M)
+    # normal equations of the first kind: conj(A) A^T w = 1_N
+    assert np.max(np.abs(np.conj(A) @ (A.T @ w) - 1.0)) < 1e-7
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_dcf_with_given_weights_matches_exact_sum(prec, tol):
+    """Hot-path parity: GPU A^*Wf against the exact sum with the same w."""
+    L, torch = lib_or_skip()
+    x = inputs.random_points(7000, 2, 41)
+    M = 32
+    w = inputs.coeffs_complex((7000,), 42) / 7000
+    f = inputs.samples_complex(7000, 43)
+    p = L.Plan(x, M, 2.0, 6, prec)
+    p.set_weights(w)
+    assert np.array_equal(p.get_weights(), w)
+    cd = torch.complex128 if prec == "fp64" else torch.complex64
+    h = p.adjoint(to_dev(torch, f, cd), mode=L.MODE_DCF).cpu().numpy()
+    ref = WT.reconstruct_exact(x, f, w, M)
+    assert rel(h, ref) < (tol if prec == "fp32" else 1e-9)
