@@ -99,6 +99,8 @@ void count_launch(int n = 1);
     } while (0)
 
 infft_status dev_alloc(infft_plan_s* p, void** ptr, size_t bytes);
+// in-place exclusive prefix sum of n ints on the device (stream ordered)
+infft_status scan_exclusive(int* data, long long n, cudaStream_t st);
 bool is_device_pointer(const void* ptr);
 
 // Build the Job descriptors of a list of plans for one transform each.

@@ -105,6 +105,119 @@ __global__ void __launch_bounds__(128) k_spread(const __grid_constant__ JobSet<R
 }
 
 // ---------------------------------------------------------------------------------------
+// Two-dimensional spreading with the accumulators in registers.  One warp per work
+// item; lane l owns column l of the item's P x P padded tile (P = T + 2m + 1 <= 32).
+// The item's points are sorted by base row, so the rows a point can touch,
+// [oy, oy + 2m] (padded coordinates; one more row for B_opt slots), only move down:
+// each lane keeps those rows of its column in registers, adds the point's taps
+// (coefficient c_j psi_y[k] broadcast, times psi_x of its column), and when the next
+// point starts lower it stores the rows that no later point can reach.  Every padded
+// cell is stored exactly once, no shared-memory read-modify-write, no atomics.
+// Window values are computed once per point while staging 32 points per warp.
+template <class R, int MM, bool BOPT>
+__global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet<R> js) {
+    constexpr int W = 2 * MM + 1;              // window taps per axis
+    constexpr int WR = BOPT ? W + 1 : W;       // rows held in registers
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gitem = blockIdx.x * js.wpb + warp;
+    if (gitem >= js.pre_items[js.njobs]) return;
+    const int jb = find_job(js.pre_items, js.njobs, gitem);
+    const Job<R>& J = js.job[jb];
+    const int it = gitem - js.pre_items[jb];
+    const int4 item = J.items[it];
+    const int P = J.P, Ms = J.Ms, T = J.T;
+
+    unsigned char* base = smem_raw + (size_t)warp * js.smem_per_warp;
+    cx<R>* cy = reinterpret_cast<cx<R>*>(base);            // [32][W]  c_j psi_y (window mode)
+    R* psx = reinterpret_cast<R*>(cy + 32 * W);             // [32][W]  psi_x
+    int* meta = reinterpret_cast<int*>(psx + 32 * W);       // [32][3]  oy, ox, sorted index
+    cx<R>* cst = reinterpret_cast<cx<R>*>(meta + 96);       // [32]     c_j (B_opt mode)
+
+    const int ty = item.x / J.ntile, tx = item.x % J.ntile;
+    R are[WR], aim[WR];
+#pragma unroll
+    for (int k = 0; k < WR; ++k) { are[k] = R(0); aim[k] = R(0); }
+    int r0 = 0;  // padded row held in are[0]
+    cx<R>* dst = J.padded + (size_t)it * P * P;
+    const bool col_ok = lane < P;
+
+    for (int c0 = 0; c0 < item.z; c0 += 32) {
+        const int np = min(32, item.z - c0);
+        __syncwarp();
+        if (lane < np) {
+            const int i = item.y + c0 + lane;
+            const int j = __ldg(J.perm + i);
+            cx<R> fv = J.in[j];
+            if (J.mode == INFFT_MODE_DCF) fv = mul(J.w[i], fv);
+            const uint32_t cl = __ldg(J.cell + i);
+            const int cxl = (int)(cl % (uint32_t)Ms), cyl = (int)(cl / (uint32_t)Ms);
+            meta[lane * 3 + 0] = cyl - ty * T;
+            meta[lane * 3 + 1] = cxl - tx * T;
+            meta[lane * 3 + 2] = i;
+            if (BOPT) {
+                cst[lane] = fv;
+            } else {
+                const R uy = J.u[(size_t)i * 2 + 0], ux = J.u[(size_t)i * 2 + 1];
+#pragma unroll
+                for (int s = 0; s < W; ++s) {
+                    const R wy = tap_weight<R>(J.window, uy, s, MM, J.inv_m, J.beta);
+                    cy[lane * W + s] = scale(fv, wy);
+                    psx[lane * W + s] = tap_weight<R>(J.window, ux, s, MM, J.inv_m, J.beta);
+                }
+            }
+        }
+        __syncwarp();
+        for (int p = 0; p < np; ++p) {
+            const int oy = meta[p * 3 + 0], ox = meta[p * 3 + 1];
+            // store the rows above oy: no later point reaches them
+            while (r0 < oy) {
+                if (col_ok) dst[(size_t)r0 * P + lane] = mk<R>(are[0], aim[0]);
+#pragma unroll
+                for (int k = 0; k < WR - 1; ++k) { are[k] = are[k + 1]; aim[k] = aim[k + 1]; }
+                are[WR - 1] = R(0);
+                aim[WR - 1] = R(0);
+                ++r0;
+            }
+            const int sx = lane - ox;
+            if (BOPT) {
+                constexpr int S = W + 1;
+                if (sx >= 0 && sx < S) {
+                    const int i = meta[p * 3 + 2];
+                    const cx<R> cv = cst[p];
+                    const cx<R>* cf = J.coef + (size_t)i * S * S + sx;
+#pragma unroll
+                    for (int k = 0; k < S; ++k) {
+                        const cx<R> b = cf[k * S];
+                        are[k] += b.re * cv.re + b.im * cv.im;   // conj(b) f
+                        aim[k] += b.re * cv.im - b.im * cv.re;
+                    }
+                }
+            } else {
+                const bool in = (sx >= 0) && (sx < W);
+                const R wx = in ? psx[p * W + (in ? sx : 0)] : R(0);
+                const cx<R>* cp = cy + p * W;
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    const cx<R> c = cp[k];
+                    are[k] += c.re * wx;
+                    aim[k] += c.im * wx;
+                }
+            }
+        }
+    }
+    // remaining rows (including rows no point reached)
+    while (r0 < P) {
+        if (col_ok) dst[(size_t)r0 * P + lane] = mk<R>(are[0], aim[0]);
+#pragma unroll
+        for (int k = 0; k < WR - 1; ++k) { are[k] = are[k + 1]; aim[k] = aim[k + 1]; }
+        are[WR - 1] = R(0);
+        aim[WR - 1] = R(0);
+        ++r0;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // merge: grid cell c receives the sum of every padded-tile cell that maps onto it
 // (padded cell o of tile tl along an axis sits at (tl T - m + o) mod Ms).  One thread per
 // grid cell, work items of a tile summed in item order: deterministic.
@@ -395,10 +508,74 @@ static size_t spread_smem_per_warp(const JobSet<R>& js, int D) {
     return mx;
 }
 
+// register-row spreading for d = 2 when every job has the same m (2..7) and P <= 32
+template <class R, int MM, bool BOPT>
+static infft_status launch_spread2d_m(JobSet<R>& js, cudaStream_t st) {
+    constexpr int W = 2 * MM + 1;
+    size_t spw = 32 * W * sizeof(cx<R>) + 32 * W * sizeof(R) + 96 * sizeof(int) + 32 * sizeof(cx<R>);
+    spw = (spw + 15) & ~(size_t)15;
+    js.smem_per_warp = (int)spw;
+    js.wpb = 4;
+    const int nitems = js.pre_items[js.njobs];
+    if (nitems == 0) return INFFT_OK;
+    const size_t smem = spw * js.wpb;
+    INFFT_CUDA(cudaFuncSetAttribute(k_spread2d<R, MM, BOPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_spread2d<R, MM, BOPT><<<(nitems + js.wpb - 1) / js.wpb, 32 * js.wpb, smem, st>>>(js);
+    INFFT_LAUNCHED();
+    return INFFT_OK;
+}
+
+template <class R, bool BOPT>
+static infft_status launch_spread2d(JobSet<R>& js, cudaStream_t st, int m) {
+    switch (m) {
+        case 2: return launch_spread2d_m<R, 2, BOPT>(js, st);
+        case 3: return launch_spread2d_m<R, 3, BOPT>(js, st);
+        case 4: return launch_spread2d_m<R, 4, BOPT>(js, st);
+        case 5: return launch_spread2d_m<R, 5, BOPT>(js, st);
+        case 6: return launch_spread2d_m<R, 6, BOPT>(js, st);
+        default: return launch_spread2d_m<R, 7, BOPT>(js, st);
+    }
+}
+
+template <class R>
+static bool spread2d_eligible(const JobSet<R>& js, int* m_out, bool* bopt_out) {
+    if (js.njobs < 1) return false;
+    const int m = js.job[0].m;
+    const bool bopt = js.job[0].mode == INFFT_MODE_BOPT;
+    for (int j = 0; j < js.njobs; ++j) {
+        const Job<R>& J = js.job[j];
+        if (J.d != 2 || J.m != m || (J.mode == INFFT_MODE_BOPT) != bopt || J.P > 32) return false;
+    }
+    if (m < 2 || m > 7) return false;
+    *m_out = m;
+    *bopt_out = bopt;
+    return true;
+}
+
 template <class R, int D>
 static infft_status launch_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* ev) {
     fill_prefixes(js, D, false);
     if (ev) INFFT_CUDA(cudaEventRecord(ev[0], st));
+    int m2 = 0;
+    bool bopt2 = false;
+    if (D == 2 && spread2d_eligible(js, &m2, &bopt2)) {
+        const infft_status s2 = bopt2 ? launch_spread2d<R, true>(js, st, m2) : launch_spread2d<R, false>(js, st, m2);
+        if (s2 != INFFT_OK) return s2;
+        if (ev) INFFT_CUDA(cudaEventRecord(ev[1], st));
+        k_merge<R, D><<<js.pre_merge[js.njobs], 256, 0, st>>>(js);
+        INFFT_LAUNCHED();
+        if (ev) INFFT_CUDA(cudaEventRecord(ev[2], st));
+        int maxMs = 0;
+        for (int j = 0; j < js.njobs; ++j) maxMs = std::max(maxMs, js.job[j].Ms);
+        const size_t fsmem = (size_t)js.L * maxMs * sizeof(cx<R>);
+        INFFT_CUDA(cudaFuncSetAttribute(k_fft<R, D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
+        for (int p = 0; p < D; ++p) {
+            k_fft<R, D, false><<<js.pre_fft[p][js.njobs], 256, fsmem, st>>>(js, p);
+            INFFT_LAUNCHED();
+            if (ev) INFFT_CUDA(cudaEventRecord(ev[3 + p], st));
+        }
+        return INFFT_OK;
+    }
     const size_t spw = spread_smem_per_warp(js, D);
     const size_t smem_cap = 200 * 1024;
     if (spw > smem_cap) {

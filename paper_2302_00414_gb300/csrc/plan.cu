@@ -115,7 +115,7 @@ __global__ void k_scan_add(int* __restrict__ data, long long n, const int* __res
     if (i < n) data[i] += block_off[blockIdx.x];
 }
 
-static infft_status scan_exclusive(int* data, long long n, cudaStream_t st) {
+infft_status scan_exclusive(int* data, long long n, cudaStream_t st) {
     const long long nb = (n + 1023) / 1024;
     if (nb == 1) {
         k_scan_block<<<1, 1024, 0, st>>>(data, n, nullptr);
