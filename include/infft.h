@@ -191,6 +191,29 @@ infft_status infft_batch_create(const infft_plan_t* plans, int count, int mode,
 infft_status infft_batch_run(infft_batch_t batch, void* stream);
 void infft_batch_destroy(infft_batch_t batch);
 
+/*
+ * infft_adjoint_noalloc -- the same reconstruction as infft_adjoint, for callers that
+ * must not allocate device memory during the call: programs whose device memory is
+ * owned by an external allocator or arena that forbids other components from calling
+ * cudaMalloc, and latency-bound loops that cannot afford cudaMalloc's synchronisation
+ * or a late out-of-memory failure.  (The paper has no counterpart; this is an interface
+ * of the library.)
+ *   plan, mode : as for infft_adjoint (the plan is created beforehand).
+ *   f, fhat    : DEVICE pointers (host pointers are rejected with INFFT_EINVAL).
+ * The per-call scratch (padded tiles, oversampled grid, FFT intermediates) lives in a
+ * fixed 32 MiB array compiled into the library, which every device that loads the
+ * library holds until the process exits.  A plan whose scratch would exceed 32 MiB is
+ * rejected with INFFT_EINVAL and a message giving both sizes.  The call allocates
+ * nothing: no cudaMalloc, no cudaFree, no allocating library routine.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current and caches it; make that first call before any stream
+ * capture.  All calls share the one array and every call overwrites all the scratch it
+ * reads, so nothing carries over between calls -- but calls that overlap on the GPU
+ * (different streams, or different host threads) race on it and must be serialised by
+ * the caller.
+ */
+infft_status infft_adjoint_noalloc(infft_plan_t plan, int mode, const void* f, void* fhat, void* stream);
+
 /* Accessors. */
 int64_t infft_plan_N(infft_plan_t plan);
 int infft_plan_Msigma(infft_plan_t plan);

@@ -51,6 +51,7 @@ _SIGS = {
     "infft_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p),
                                      C.POINTER(C.c_void_p), C.c_void_p, C.POINTER(C.c_void_p)]),
     "infft_batch_run": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "infft_adjoint_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "infft_batch_destroy": (None, [C.c_void_p]),
     "infft_plan_N": (C.c_int64, [C.c_void_p]),
     "infft_plan_Msigma": (C.c_int, [C.c_void_p]),
@@ -119,6 +120,12 @@ def infft_optimize_B(plan, opts=0, stream=0):
 
 def infft_adjoint(plan, mode, f_ptr, fhat_ptr, stream=0):
     return load().infft_adjoint(plan, mode, f_ptr, fhat_ptr, stream)
+
+
+def infft_adjoint_noalloc(plan, mode, f_ptr, fhat_ptr, stream=0):
+    """The reconstruction of infft_adjoint with the per-call scratch in the library's
+    fixed device array (device pointers only; see include/infft.h)."""
+    return load().infft_adjoint_noalloc(plan, mode, f_ptr, fhat_ptr, stream)
 
 
 def infft_forward(plan, fhat_ptr, f_ptr, stream=0):

@@ -35,6 +35,7 @@ struct infft_plan_s {
     void* dinv = nullptr;     // M entries
     void* tw = nullptr;       // Ms/2 complex
     void* dinv_win = nullptr; // M entries for the B_opt window (may alias dinv)
+    float* wpoly = nullptr;   // window polynomial table (float32 Kaiser-Bessel plans)
 
     // weights (device): caller order float64 master + sorted copy in plan precision
     void* w_master = nullptr; // N complex128, caller order
@@ -114,5 +115,7 @@ Job<R> make_job(const infft_plan_s* p, int mode, const void* in, void* out);
 // spread and after the spread, the merge and each FFT pass.
 template <class R>
 infft_status run_jobs(const std::vector<Job<R>>& jobs, cudaStream_t st, bool forward, cudaEvent_t* ev = nullptr);
+template <class R>
+infft_status run_jobs(const Job<R>* jobs, size_t count, cudaStream_t st, bool forward, cudaEvent_t* ev = nullptr);
 
 }  // namespace infft

@@ -117,7 +117,9 @@ __global__ void __launch_bounds__(128) k_spread(const __grid_constant__ JobSet<R
 template <class R, int MM, bool BOPT>
 __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet<R> js) {
     constexpr int W = 2 * MM + 1;              // window taps per axis
+    constexpr int WE = W + 1;                  // even stride of the staged rows (16-byte loads)
     constexpr int WR = BOPT ? W + 1 : W;       // rows held in registers
+    constexpr bool F32 = sizeof(R) == 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gitem = blockIdx.x * js.wpb + warp;
@@ -129,10 +131,15 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
     const int P = J.P, Ms = J.Ms, T = J.T;
 
     unsigned char* base = smem_raw + (size_t)warp * js.smem_per_warp;
-    cx<R>* cy = reinterpret_cast<cx<R>*>(base);            // [32][W]  c_j psi_y (window mode)
-    R* psx = reinterpret_cast<R*>(cy + 32 * W);             // [32][W]  psi_x
-    int* meta = reinterpret_cast<int*>(psx + 32 * W);       // [32][3]  oy, ox, sorted index
+    cx<R>* cy = reinterpret_cast<cx<R>*>(base);            // [32][WE] c_j psi_y (window mode)
+    R* psx = reinterpret_cast<R*>(cy + 32 * WE);            // [32][WE] psi_x
+    int* meta = reinterpret_cast<int*>(psx + 32 * WE);      // [32][3]  oy, ox, sorted index
     cx<R>* cst = reinterpret_cast<cx<R>*>(meta + 96);       // [32]     c_j (B_opt mode)
+    float* poly = reinterpret_cast<float*>(cst + 32);       // [(WPOLY_DEG+1) * W] window polynomial
+    const bool use_poly = F32 && !BOPT && J.wpoly != nullptr;
+    if (use_poly) {
+        for (int e = lane; e < (WPOLY_DEG + 1) * W; e += 32) poly[e] = J.wpoly[e];
+    }
 
     const int ty = item.x / J.ntile, tx = item.x % J.ntile;
     R are[WR], aim[WR];
@@ -159,12 +166,28 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
                 cst[lane] = fv;
             } else {
                 const R uy = J.u[(size_t)i * 2 + 0], ux = J.u[(size_t)i * 2 + 1];
+                R wy[W], wx[W];
+                bool done = false;
+                if constexpr (F32) {
+                    if (use_poly) {
+                        poly_taps<W>(poly, uy, wy);
+                        poly_taps<W>(poly, ux, wx);
+                        done = true;
+                    }
+                }
+                if (!done) {
+#pragma unroll
+                    for (int s = 0; s < W; ++s) {
+                        wy[s] = tap_weight<R>(J.window, uy, s, MM, J.inv_m, J.beta);
+                        wx[s] = tap_weight<R>(J.window, ux, s, MM, J.inv_m, J.beta);
+                    }
+                }
 #pragma unroll
                 for (int s = 0; s < W; ++s) {
-                    const R wy = tap_weight<R>(J.window, uy, s, MM, J.inv_m, J.beta);
-                    cy[lane * W + s] = scale(fv, wy);
-                    psx[lane * W + s] = tap_weight<R>(J.window, ux, s, MM, J.inv_m, J.beta);
+                    cy[lane * WE + s] = scale(fv, wy[s]);
+                    psx[lane * WE + s] = wx[s];
                 }
+                cy[lane * WE + W] = mk<R>(0, 0);
             }
         }
         __syncwarp();
@@ -195,13 +218,28 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
                 }
             } else {
                 const bool in = (sx >= 0) && (sx < W);
-                const R wx = in ? psx[p * W + (in ? sx : 0)] : R(0);
-                const cx<R>* cp = cy + p * W;
+                const R wx = in ? psx[p * WE + (in ? sx : 0)] : R(0);
+                const cx<R>* cp = cy + p * WE;
+                if constexpr (F32) {
+                    // two complex coefficients per 16-byte broadcast load
+                    const float4* cp4 = reinterpret_cast<const float4*>(cp);
 #pragma unroll
-                for (int k = 0; k < W; ++k) {
-                    const cx<R> c = cp[k];
-                    are[k] += c.re * wx;
-                    aim[k] += c.im * wx;
+                    for (int k2 = 0; k2 < WE / 2; ++k2) {
+                        const float4 c = cp4[k2];
+                        are[2 * k2] += c.x * wx;
+                        aim[2 * k2] += c.y * wx;
+                        if (2 * k2 + 1 < W) {
+                            are[2 * k2 + 1] += c.z * wx;
+                            aim[2 * k2 + 1] += c.w * wx;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < W; ++k) {
+                        const cx<R> c = cp[k];
+                        are[k] += c.re * wx;
+                        aim[k] += c.im * wx;
+                    }
                 }
             }
         }
@@ -512,7 +550,9 @@ static size_t spread_smem_per_warp(const JobSet<R>& js, int D) {
 template <class R, int MM, bool BOPT>
 static infft_status launch_spread2d_m(JobSet<R>& js, cudaStream_t st) {
     constexpr int W = 2 * MM + 1;
-    size_t spw = 32 * W * sizeof(cx<R>) + 32 * W * sizeof(R) + 96 * sizeof(int) + 32 * sizeof(cx<R>);
+    constexpr int WE = W + 1;
+    size_t spw = 32 * WE * sizeof(cx<R>) + 32 * WE * sizeof(R) + 96 * sizeof(int) + 32 * sizeof(cx<R>) +
+                 (WPOLY_DEG + 1) * W * sizeof(float);
     spw = (spw + 15) & ~(size_t)15;
     js.smem_per_warp = (int)spw;
     js.wpb = 4;
@@ -643,12 +683,17 @@ static infft_status launch_forward(JobSet<R>& js, cudaStream_t st) {
 
 template <class R>
 infft_status run_jobs(const std::vector<Job<R>>& jobs, cudaStream_t st, bool forward, cudaEvent_t* ev) {
-    if (jobs.empty()) return INFFT_OK;
+    return run_jobs<R>(jobs.data(), jobs.size(), st, forward, ev);
+}
+
+template <class R>
+infft_status run_jobs(const Job<R>* jobs, size_t count, cudaStream_t st, bool forward, cudaEvent_t* ev) {
+    if (count == 0) return INFFT_OK;
     const int D = jobs[0].d;
-    for (size_t s = 0; s < jobs.size(); s += MAXJ) {
+    for (size_t s = 0; s < count; s += MAXJ) {
         JobSet<R> js;
         memset(&js, 0, sizeof(js));
-        js.njobs = (int)std::min<size_t>(MAXJ, jobs.size() - s);
+        js.njobs = (int)std::min<size_t>(MAXJ, count - s);
         for (int j = 0; j < js.njobs; ++j) js.job[j] = jobs[s + j];
         infft_status r;
         if (!forward) {
@@ -664,5 +709,7 @@ infft_status run_jobs(const std::vector<Job<R>>& jobs, cudaStream_t st, bool for
 
 template infft_status run_jobs<float>(const std::vector<Job<float>>&, cudaStream_t, bool, cudaEvent_t*);
 template infft_status run_jobs<double>(const std::vector<Job<double>>&, cudaStream_t, bool, cudaEvent_t*);
+template infft_status run_jobs<float>(const Job<float>*, size_t, cudaStream_t, bool, cudaEvent_t*);
+template infft_status run_jobs<double>(const Job<double>*, size_t, cudaStream_t, bool, cudaEvent_t*);
 
 }  // namespace infft

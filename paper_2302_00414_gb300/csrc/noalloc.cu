@@ -1,0 +1,108 @@
+// infft_adjoint_noalloc: the reconstruction of infft_adjoint with its per-call scratch
+// (padded tiles, oversampled grid, FFT intermediates) taken from one fixed array that
+// is part of the library image, so that the call itself allocates no device memory.
+//
+// Who needs this: applications whose device memory is owned by an external allocator
+// or arena that forbids other components from calling cudaMalloc, and latency-bound
+// loops that cannot afford cudaMalloc's synchronisation or its late out-of-memory
+// failures.  Such callers create their plans up front, then reconstruct through this
+// entry point with buffers they already own.
+#include <mutex>
+
+#include "internal.h"
+
+// 32 MiB of scratch per device, reserved for the lifetime of the process on every
+// device that loads the library.
+#define INFFT_NOALLOC_SCRATCH_BYTES (32ull << 20)
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[INFFT_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mutex;
+void* g_scratch_addr[kMaxDevices] = {nullptr};
+
+// Device address of g_noalloc_scratch on the current device.  In host code the
+// symbol only names a host-side stand-in, so its address is looked up once per
+// device, with that device current, and cached.
+infft_status scratch_address(void** out) {
+    int dev = 0;
+    INFFT_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        infft::set_error("device index %d out of range", dev);
+        return INFFT_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            infft::set_error("cudaGetSymbolAddress(g_noalloc_scratch) failed: %s", cudaGetErrorString(e));
+            return INFFT_ECUDA;
+        }
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return INFFT_OK;
+}
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+template <class R>
+infft_status run(infft_plan_s* p, int mode, const void* f, void* fhat, cudaStream_t st) {
+    using infft::cx;
+    const int d = p->d;
+    size_t cells_p = 1, grid = 1;
+    for (int t = 0; t < d; ++t) { cells_p *= (size_t)p->P; grid *= (size_t)p->Ms; }
+    size_t t1 = 0, t2 = 0;
+    if (d >= 2) t1 = (size_t)infft::ipow(p->Ms, d - 1) * p->M;
+    if (d == 3) t2 = (size_t)p->Ms * p->M * p->M;
+    const size_t C = sizeof(cx<R>);
+    const size_t b_pad = round256(std::max<size_t>(1, (size_t)p->nitems) * cells_p * C);
+    const size_t b_grid = round256(grid * C);
+    const size_t b_t1 = round256(t1 * C), b_t2 = round256(t2 * C);
+    const size_t need = b_pad + b_grid + b_t1 + b_t2;
+    if (need > INFFT_NOALLOC_SCRATCH_BYTES) {
+        infft::set_error("infft_adjoint_noalloc: plan needs %zu bytes of scratch, the fixed array holds %llu",
+                         need, (unsigned long long)INFFT_NOALLOC_SCRATCH_BYTES);
+        return INFFT_EINVAL;
+    }
+    void* base = nullptr;
+    INFFT_TRY(scratch_address(&base));
+    unsigned char* s = static_cast<unsigned char*>(base);
+    infft::Job<R> job = infft::make_job<R>(p, mode, f, fhat);
+    job.padded = reinterpret_cast<cx<R>*>(s);
+    job.grid = reinterpret_cast<cx<R>*>(s + b_pad);
+    job.tmp1 = t1 ? reinterpret_cast<cx<R>*>(s + b_pad + b_grid) : nullptr;
+    job.tmp2 = t2 ? reinterpret_cast<cx<R>*>(s + b_pad + b_grid + b_t1) : nullptr;
+    // Every scratch cell is written before it is read (the spread stores whole padded
+    // tiles, the merge every grid cell, each FFT pass its whole output), so nothing left
+    // by an earlier call needs clearing.
+    return infft::run_jobs<R>(&job, 1, st, false, nullptr);
+}
+
+}  // namespace
+
+extern "C" {
+
+infft_status infft_adjoint_noalloc(infft_plan_t plan, int mode, const void* f, void* fhat, void* stream) {
+    if (!plan || !f || !fhat) {
+        infft::set_error("infft_adjoint_noalloc: null argument");
+        return INFFT_EINVAL;
+    }
+    if (mode == INFFT_MODE_DCF && !plan->has_weights) { infft::set_error("DCF mode needs weights"); return INFFT_ESTATE; }
+    if (mode == INFFT_MODE_BOPT && !plan->has_bopt) { infft::set_error("BOPT mode needs B_opt"); return INFFT_ESTATE; }
+    if (mode < 0 || mode > 2 || (mode != INFFT_MODE_BOPT && plan->window == infft::WK_DIRICHLET)) {
+        infft::set_error("infft_adjoint_noalloc: mode %d not valid for this plan", mode);
+        return INFFT_EINVAL;
+    }
+    if (!infft::is_device_pointer(f) || !infft::is_device_pointer(fhat)) {
+        infft::set_error("infft_adjoint_noalloc: f and fhat must be device pointers");
+        return INFFT_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    return plan->fp64 ? run<double>(plan, mode, f, fhat, st) : run<float>(plan, mode, f, fhat, st);
+}
+
+}  // extern "C"
