@@ -96,6 +96,27 @@ __device__ __forceinline__ R tap_weight(int kind, R u, int s, int m, R inv_m, R 
     return window_phi<R>(kind, u + R(m - s), m, inv_m, beta);
 }
 
+// Float32 plans evaluate the Kaiser-Bessel taps s = 1..2m from per-plan polynomials:
+// phi(u + m - s) = sum_k c[k][s] v^k, v = 2u - 1, u in [0, 1], degree WPOLY_DEG, obtained
+// by Chebyshev interpolation in float64 at plan creation (piecewise-polynomial kernel
+// evaluation in the manner of Barnett, Magland and af Klinteberg, SIAM J. Sci. Comput.
+// 2019).  Degree 10 reaches the float32 rounding level of the window.  Tap 0 keeps the
+// exact membership rule: I0(0) = 1 on a grid node, 0 otherwise.
+constexpr int WPOLY_DEG = 10;
+
+template <int W>
+__device__ __forceinline__ void poly_taps(const float* __restrict__ c, float u, float* out) {
+    const float v = 2.f * u - 1.f;
+#pragma unroll
+    for (int s = 1; s < W; ++s) out[s] = c[WPOLY_DEG * W + s];
+#pragma unroll
+    for (int k = WPOLY_DEG - 1; k >= 0; --k) {
+#pragma unroll
+        for (int s = 1; s < W; ++s) out[s] = fmaf(out[s], v, c[k * W + s]);
+    }
+    out[0] = (u == 0.f) ? 1.f : 0.f;
+}
+
 // ----------------------------------------------------------------------------------------
 // Work descriptors.  One Job describes one transform (one plan, one in/out pair);
 // kernels receive an array of Jobs with the same d and precision and map their
@@ -116,6 +137,7 @@ struct Job {
     const int4* items;         // (tile, start, count, 0)
     const int* tile_items;     // ntile^d + 1 prefix of items per tile
     const R* dinv;             // M entries 1/(Ms w^(k)) (per axis)
+    const float* wpoly;        // (WPOLY_DEG + 1) x (2m+1) window polynomial (float32 KB plans) or null
     const cx<R>* tw;           // Ms/2 twiddles exp(-2 pi i k / Ms)
     cx<R>* padded;             // nitems * P^d
     cx<R>* grid;               // Ms^d

@@ -204,6 +204,42 @@ __global__ void k_tables(int M, int Ms, int m, int window, double beta, R* __res
     }
 }
 
+// Window polynomials for float32 Kaiser-Bessel plans: one thread per tap s = 1..2m
+// interpolates phi(u + m - s), u in [0,1], at the WPOLY_DEG+1 Chebyshev points of
+// v = 2u - 1 and rewrites the Chebyshev series in powers of v (float64 throughout).
+__global__ void k_wpoly(int m, double beta, float* __restrict__ coef) {
+    constexpr int P1 = WPOLY_DEG + 1;
+    const int W = 2 * m + 1;
+    const int s = threadIdx.x;
+    if (s >= W) return;
+    if (s == 0) {
+        for (int k = 0; k < P1; ++k) coef[k * W] = 0.f;
+        return;
+    }
+    double fv[P1], c[P1], a[P1], tp[P1], tc[P1], tn[P1];
+    for (int k = 0; k < P1; ++k) {
+        const double v = cospi((k + 0.5) / P1);
+        const double u = 0.5 * (v + 1.0);
+        fv[k] = kb_phi<double>(u + (double)(m - s), 1.0 / m, beta);
+    }
+    for (int j = 0; j < P1; ++j) {
+        double acc = 0;
+        for (int k = 0; k < P1; ++k) acc += fv[k] * cospi(j * (k + 0.5) / P1);
+        c[j] = acc * 2.0 / P1;
+    }
+    c[0] *= 0.5;
+    for (int k = 0; k < P1; ++k) { a[k] = 0; tp[k] = 0; tc[k] = 0; }
+    tp[0] = 1.0;          // T_0
+    tc[1] = 1.0;          // T_1
+    for (int k = 0; k < P1; ++k) a[k] += c[0] * tp[k] + c[1] * tc[k];
+    for (int j = 2; j < P1; ++j) {
+        // T_j = 2 v T_{j-1} - T_{j-2}
+        for (int k = 0; k < P1; ++k) tn[k] = -tp[k] + ((k > 0) ? 2.0 * tc[k - 1] : 0.0);
+        for (int k = 0; k < P1; ++k) { a[k] += c[j] * tn[k]; tp[k] = tc[k]; tc[k] = tn[k]; }
+    }
+    for (int k = 0; k < P1; ++k) coef[k * W + s] = (float)a[k];
+}
+
 // ----------------------------------------------------------------------------------------
 template <class R>
 Job<R> make_job(const infft_plan_s* p, int mode, const void* in, void* out) {
@@ -218,6 +254,7 @@ Job<R> make_job(const infft_plan_s* p, int mode, const void* in, void* out) {
     J.items = p->items; J.tile_items = p->tile_items;
     J.dinv = (mode == INFFT_MODE_BOPT && p->dinv_win) ? (const R*)p->dinv_win : (const R*)p->dinv;
     J.tw = (const cx<R>*)p->tw;
+    J.wpoly = p->wpoly;
     J.padded = (cx<R>*)p->padded; J.grid = (cx<R>*)p->grid;
     J.tmp1 = (cx<R>*)p->tmp1; J.tmp2 = (cx<R>*)p->tmp2;
     J.in = (const cx<R>*)in; J.out = (cx<R>*)out;
@@ -230,7 +267,7 @@ static void free_plan(infft_plan_s* p) {
     if (!p) return;
     void* ptrs[] = {p->perm, p->cell, p->u, p->x64, p->items, p->tile_items, p->cell_start, p->dinv, p->tw,
                     p->dinv_win, p->w_master, p->w_sorted, p->coef, p->coef64, p->padded, p->grid, p->tmp1,
-                    p->tmp2, p->io_in, p->io_out};
+                    p->tmp2, p->io_in, p->io_out, p->wpoly};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -343,6 +380,13 @@ static infft_status build_plan(infft_plan_s* p, const double* x_in, cudaStream_t
         k_tables<float><<<(nt + 255) / 256, 256, 0, st>>>(p->M, Ms, m, p->window, p->beta, (float*)p->dinv,
                                                          (cx<float>*)p->tw, nullptr);
     INFFT_LAUNCHED();
+
+    // window polynomials (float32 Kaiser-Bessel plans)
+    if (!p->fp64 && p->window == WK_KB && 2 * m + 1 <= 32) {
+        INFFT_TRY(dev_alloc(p, (void**)&p->wpoly, (size_t)(WPOLY_DEG + 1) * (2 * m + 1) * sizeof(float)));
+        k_wpoly<<<1, 32, 0, st>>>(m, p->beta, p->wpoly);
+        INFFT_LAUNCHED();
+    }
 
     // scratch
     long long pd = 1, msd_ = 1;
