@@ -18,6 +18,7 @@ struct JobSet {
     int wpb;                    // warps (items) per block of the spread / interpolation kernels
     int smem_per_warp;          // bytes of shared memory per warp (spread / interpolation)
     int L;                      // lines per block of the FFT passes
+    int fuse_merge;             // adjoint: first FFT pass gathers the padded tiles
     int pre_items[MAXJ + 1];    // prefix of work items
     int pre_merge[MAXJ + 1];    // prefix of merge blocks
     int pre_fft[3][MAXJ + 1];   // prefix of FFT blocks per pass

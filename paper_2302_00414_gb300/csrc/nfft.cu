@@ -255,6 +255,9 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
     }
 }
 
+template <class R, int D>
+__device__ __forceinline__ cx<R> merged_cell(const Job<R>& J, long long cidx);
+
 // ---------------------------------------------------------------------------------------
 // merge: grid cell c receives the sum of every padded-tile cell that maps onto it
 // (padded cell o of tile tl along an axis sits at (tl T - m + o) mod Ms).  One thread per
@@ -268,6 +271,13 @@ __global__ void __launch_bounds__(256) k_merge(const __grid_constant__ JobSet<R>
     const long long total = (long long)ipow(Ms, D);
     const long long cidx = (long long)(gblk - js.pre_merge[jb]) * blockDim.x + threadIdx.x;
     if (cidx >= total) return;
+    J.grid[cidx] = merged_cell<R, D>(J, cidx);
+}
+
+// Sum of every padded-tile cell that maps onto grid cell `cidx` (row-major over Ms^D).
+template <class R, int D>
+__device__ __forceinline__ cx<R> merged_cell(const Job<R>& J, long long cidx) {
+    const int Ms = J.Ms, T = J.T, m = J.m, P = J.P, nt = J.ntile;
     int c[D];
     {
         long long rem = cidx;
@@ -310,7 +320,7 @@ __global__ void __launch_bounds__(256) k_merge(const __grid_constant__ JobSet<R>
         }
         if (t < 0) break;
     }
-    J.grid[cidx] = acc;
+    return acc;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -320,6 +330,10 @@ __global__ void __launch_bounds__(256) k_merge(const __grid_constant__ JobSet<R>
 // 1/(Ms w^(k)) of this axis.  Forward direction (FWD = true): the M inputs of I_M times
 // 1/(Ms w^(k)) are placed at k mod Ms, the rest is zero, inverse DFT (sign +).
 // A pass sees a tensor (A, n_in, B): lines run along the middle index with stride B.
+// Shared-memory position of element i of a line: one padding slot every 16 elements,
+// so that the bit-reversed scatter and the short butterfly strides spread over banks.
+__device__ __forceinline__ int skew(int i) { return i + (i >> 4); }
+
 template <class R, int D, bool FWD>
 __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> js, int pass) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -333,10 +347,13 @@ __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> j
     const long long A = ipow(Ms, t);
     const long long B = ipow(M, D - 1 - t);
     const int n = Ms;
+    const int ns = n + (n >> 4);    // skewed line stride
     const int logn = 31 - __clz(n);
     const long long nlines = A * B;
     const long long q0 = (long long)lb * L;
     const bool lanes_b = (B >= L);  // consecutive lines are consecutive b: coalesce along b
+    // the adjoint's first pass gathers the padded tiles itself (no separate merge)
+    const bool gather = !FWD && pass == 0 && js.fuse_merge;
 
     const cx<R>* src;
     cx<R>* dst;
@@ -352,46 +369,48 @@ __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> j
     if (!FWD) {
         for (int e = tid; e < L * n; e += nth) {
             int l, i;
-            if (lanes_b) { l = e % L; i = e / L; } else { i = e % n; l = e / n; }
+            if (lanes_b) { l = e % L; i = e / L; } else { i = e & (n - 1); l = e >> logn; }
             const long long q = q0 + l;
             cx<R> v = mk<R>(0, 0);
             if (q < nlines) {
-                const long long a = q / B, b = q % B;
-                v = src[(a * n + i) * B + b];
+                const long long a = q / B, b = q - a * B;
+                const long long g = (a * n + i) * B + b;
+                v = gather ? merged_cell<R, D>(J, g) : src[g];
             }
-            buf[l * n + bitrev(i, logn)] = v;
+            buf[l * ns + skew(bitrev(i, logn))] = v;
         }
     } else {
-        for (int e = tid; e < L * n; e += nth) buf[e] = mk<R>(0, 0);
+        for (int e = tid; e < L * ns; e += nth) buf[e] = mk<R>(0, 0);
         __syncthreads();
         for (int e = tid; e < L * M; e += nth) {
             int l, i;
             if (lanes_b) { l = e % L; i = e / L; } else { i = e % M; l = e / M; }
             const long long q = q0 + l;
             if (q < nlines) {
-                const long long a = q / B, b = q % B;
+                const long long a = q / B, b = q - a * B;
                 const cx<R> v = scale(src[(a * M + i) * B + b], J.dinv[i]);
                 const int bin = mod_pos(i - M / 2, Ms);
-                buf[l * n + bitrev(bin, logn)] = v;
+                buf[l * ns + skew(bitrev(bin, logn))] = v;
             }
         }
     }
     __syncthreads();
 
     const int half_n = n >> 1;
-    for (int len = 2; len <= n; len <<= 1) {
-        const int half = len >> 1;
-        const int tws = n / len;
+    const int loghn = logn - 1;
+    for (int lh = 0; lh < logn; ++lh) {   // butterflies of half-length 2^lh
+        const int half = 1 << lh;
         for (int e = tid; e < L * half_n; e += nth) {
-            const int l = e / half_n, jj = e % half_n;
-            const int grp = jj / half, pos = jj % half;
-            const int i1 = l * n + grp * len + pos, i2 = i1 + half;
-            cx<R> w = J.tw[pos * tws];
+            const int l = e >> loghn, jj = e & (half_n - 1);
+            const int grp = jj >> lh, pos = jj & (half - 1);
+            const int i1 = grp * (half << 1) + pos, i2 = i1 + half;
+            cx<R> w = J.tw[pos << (loghn - lh)];
             if (FWD) w.im = -w.im;
-            const cx<R> a = buf[i1];
-            const cx<R> b = mul(w, buf[i2]);
-            buf[i1] = add(a, b);
-            buf[i2] = sub(a, b);
+            cx<R>* row = buf + l * ns;
+            const cx<R> a = row[skew(i1)];
+            const cx<R> b = mul(w, row[skew(i2)]);
+            row[skew(i1)] = add(a, b);
+            row[skew(i2)] = sub(a, b);
         }
         __syncthreads();
     }
@@ -402,19 +421,19 @@ __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> j
             if (lanes_b) { l = e % L; i = e / L; } else { i = e % M; l = e / M; }
             const long long q = q0 + l;
             if (q < nlines) {
-                const long long a = q / B, b = q % B;
+                const long long a = q / B, b = q - a * B;
                 const int bin = mod_pos(i - M / 2, Ms);
-                dst[(a * M + i) * B + b] = scale(buf[l * n + bin], J.dinv[i]);
+                dst[(a * M + i) * B + b] = scale(buf[l * ns + skew(bin)], J.dinv[i]);
             }
         }
     } else {
         for (int e = tid; e < L * n; e += nth) {
             int l, i;
-            if (lanes_b) { l = e % L; i = e / L; } else { i = e % n; l = e / n; }
+            if (lanes_b) { l = e % L; i = e / L; } else { i = e & (n - 1); l = e >> logn; }
             const long long q = q0 + l;
             if (q < nlines) {
-                const long long a = q / B, b = q % B;
-                dst[(a * n + i) * B + b] = buf[l * n + i];
+                const long long a = q / B, b = q - a * B;
+                dst[(a * n + i) * B + b] = buf[l * ns + skew(i)];
             }
         }
     }
@@ -602,12 +621,11 @@ static infft_status launch_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* 
         const infft_status s2 = bopt2 ? launch_spread2d<R, true>(js, st, m2) : launch_spread2d<R, false>(js, st, m2);
         if (s2 != INFFT_OK) return s2;
         if (ev) INFFT_CUDA(cudaEventRecord(ev[1], st));
-        k_merge<R, D><<<js.pre_merge[js.njobs], 256, 0, st>>>(js);
-        INFFT_LAUNCHED();
+        js.fuse_merge = 1;  // the first FFT pass gathers the padded tiles
         if (ev) INFFT_CUDA(cudaEventRecord(ev[2], st));
         int maxMs = 0;
         for (int j = 0; j < js.njobs; ++j) maxMs = std::max(maxMs, js.job[j].Ms);
-        const size_t fsmem = (size_t)js.L * maxMs * sizeof(cx<R>);
+        const size_t fsmem = (size_t)js.L * (maxMs + maxMs / 16) * sizeof(cx<R>);
         INFFT_CUDA(cudaFuncSetAttribute(k_fft<R, D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
         for (int p = 0; p < D; ++p) {
             k_fft<R, D, false><<<js.pre_fft[p][js.njobs], 256, fsmem, st>>>(js, p);
@@ -632,12 +650,11 @@ static infft_status launch_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* 
         INFFT_LAUNCHED();
     }
     if (ev) INFFT_CUDA(cudaEventRecord(ev[1], st));
-    k_merge<R, D><<<js.pre_merge[js.njobs], 256, 0, st>>>(js);
-    INFFT_LAUNCHED();
+    js.fuse_merge = 1;  // the first FFT pass gathers the padded tiles
     if (ev) INFFT_CUDA(cudaEventRecord(ev[2], st));
     int maxMs = 0;
     for (int j = 0; j < js.njobs; ++j) maxMs = std::max(maxMs, js.job[j].Ms);
-    const size_t fsmem = (size_t)js.L * maxMs * sizeof(cx<R>);
+    const size_t fsmem = (size_t)js.L * (maxMs + maxMs / 16) * sizeof(cx<R>);
     INFFT_CUDA(cudaFuncSetAttribute(k_fft<R, D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
     for (int p = 0; p < D; ++p) {
         k_fft<R, D, false><<<js.pre_fft[p][js.njobs], 256, fsmem, st>>>(js, p);
@@ -652,7 +669,7 @@ static infft_status launch_forward(JobSet<R>& js, cudaStream_t st) {
     fill_prefixes(js, D, true);
     int maxMs = 0;
     for (int j = 0; j < js.njobs; ++j) maxMs = std::max(maxMs, js.job[j].Ms);
-    const size_t fsmem = (size_t)js.L * maxMs * sizeof(cx<R>);
+    const size_t fsmem = (size_t)js.L * (maxMs + maxMs / 16) * sizeof(cx<R>);
     INFFT_CUDA(cudaFuncSetAttribute(k_fft<R, D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
     for (int p = 0; p < D; ++p) {
         k_fft<R, D, true><<<js.pre_fft[p][js.njobs], 256, fsmem, st>>>(js, p);
