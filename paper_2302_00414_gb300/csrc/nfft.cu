@@ -259,6 +259,42 @@ template <class R, int D>
 __device__ __forceinline__ cx<R> merged_cell(const Job<R>& J, long long cidx);
 
 // ---------------------------------------------------------------------------------------
+// Two-dimensional merge, one block per tile of T x T cells (T <= 16, T > m, Ms a multiple
+// of T), one thread per cell.  Along an axis, the cell at offset r in tile t lies in the
+// padded tile of t at r + m, of t - 1 at r + T + m when r <= m, and of t + 1 at
+// r - T + m when r >= T - m (tile indices mod ntile): at most two sources per axis.
+template <class R>
+__global__ void __launch_bounds__(256) k_merge2d(const __grid_constant__ JobSet<R> js) {
+    const int gblk = blockIdx.x;
+    const int jb = find_job(js.pre_merge, js.njobs, gblk);
+    const Job<R>& J = js.job[jb];
+    const int T = J.T, m = J.m, P = J.P, nt = J.ntile, Ms = J.Ms;
+    const int tile = gblk - js.pre_merge[jb];
+    const int ty = tile / nt, tx = tile - ty * nt;
+    const int r = threadIdx.x >> 4, c = threadIdx.x & 15;
+    if (r >= T || c >= T) return;
+    int yt[2], yo[2], xt[2], xo[2];
+    int ny = 1, nx = 1;
+    yt[0] = ty; yo[0] = r + m;
+    xt[0] = tx; xo[0] = c + m;
+    if (r <= m) { yt[1] = (ty - 1 + nt) % nt; yo[1] = r + T + m; ny = 2; }
+    else if (r >= T - m) { yt[1] = (ty + 1) % nt; yo[1] = r - T + m; ny = 2; }
+    if (c <= m) { xt[1] = (tx - 1 + nt) % nt; xo[1] = c + T + m; nx = 2; }
+    else if (c >= T - m) { xt[1] = (tx + 1) % nt; xo[1] = c - T + m; nx = 2; }
+    const size_t cells = (size_t)P * P;
+    cx<R> acc = mk<R>(0, 0);
+    for (int a = 0; a < ny; ++a) {
+        for (int b = 0; b < nx; ++b) {
+            const int tl = yt[a] * nt + xt[b];
+            const int i0 = J.tile_items[tl], i1 = J.tile_items[tl + 1];
+            const size_t off = (size_t)yo[a] * P + xo[b];
+            for (int itm = i0; itm < i1; ++itm) acc = add(acc, J.padded[(size_t)itm * cells + off]);
+        }
+    }
+    J.grid[(size_t)(ty * T + r) * Ms + tx * T + c] = acc;
+}
+
+// ---------------------------------------------------------------------------------------
 // merge: grid cell c receives the sum of every padded-tile cell that maps onto it
 // (padded cell o of tile tl along an axis sits at (tl T - m + o) mod Ms).  One thread per
 // grid cell, work items of a tile summed in item order: deterministic.
@@ -352,8 +388,6 @@ __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> j
     const long long nlines = A * B;
     const long long q0 = (long long)lb * L;
     const bool lanes_b = (B >= L);  // consecutive lines are consecutive b: coalesce along b
-    // the adjoint's first pass gathers the padded tiles itself (no separate merge)
-    const bool gather = !FWD && pass == 0 && js.fuse_merge;
 
     const cx<R>* src;
     cx<R>* dst;
@@ -375,7 +409,7 @@ __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> j
             if (q < nlines) {
                 const long long a = q / B, b = q - a * B;
                 const long long g = (a * n + i) * B + b;
-                v = gather ? merged_cell<R, D>(J, g) : src[g];
+                v = src[g];
             }
             buf[l * ns + skew(bitrev(i, logn))] = v;
         }
@@ -621,7 +655,11 @@ static infft_status launch_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* 
         const infft_status s2 = bopt2 ? launch_spread2d<R, true>(js, st, m2) : launch_spread2d<R, false>(js, st, m2);
         if (s2 != INFFT_OK) return s2;
         if (ev) INFFT_CUDA(cudaEventRecord(ev[1], st));
-        js.fuse_merge = 1;  // the first FFT pass gathers the padded tiles
+        // merge: one block per tile
+        js.pre_merge[0] = 0;
+        for (int j = 0; j < js.njobs; ++j) js.pre_merge[j + 1] = js.pre_merge[j] + js.job[j].ntile * js.job[j].ntile;
+        k_merge2d<R><<<js.pre_merge[js.njobs], 256, 0, st>>>(js);
+        INFFT_LAUNCHED();
         if (ev) INFFT_CUDA(cudaEventRecord(ev[2], st));
         int maxMs = 0;
         for (int j = 0; j < js.njobs; ++j) maxMs = std::max(maxMs, js.job[j].Ms);
@@ -650,7 +688,8 @@ static infft_status launch_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* 
         INFFT_LAUNCHED();
     }
     if (ev) INFFT_CUDA(cudaEventRecord(ev[1], st));
-    js.fuse_merge = 1;  // the first FFT pass gathers the padded tiles
+    k_merge<R, D><<<js.pre_merge[js.njobs], 256, 0, st>>>(js);
+    INFFT_LAUNCHED();
     if (ev) INFFT_CUDA(cudaEventRecord(ev[2], st));
     int maxMs = 0;
     for (int j = 0; j < js.njobs; ++j) maxMs = std::max(maxMs, js.job[j].Ms);
