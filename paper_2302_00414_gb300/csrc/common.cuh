@@ -104,17 +104,51 @@ __device__ __forceinline__ R tap_weight(int kind, R u, int s, int m, R inv_m, R 
 // exact membership rule: I0(0) = 1 on a grid node, 0 otherwise.
 constexpr int WPOLY_DEG = 10;
 
+// row stride of the coefficient table: taps padded to a multiple of 4 (16-byte rows)
+__host__ __device__ constexpr int wpoly_stride(int W) { return (W + 3) & ~3; }
+
 template <int W>
 __device__ __forceinline__ void poly_taps(const float* __restrict__ c, float u, float* out) {
+    constexpr int WP = wpoly_stride(W);
     const float v = 2.f * u - 1.f;
 #pragma unroll
-    for (int s = 1; s < W; ++s) out[s] = c[WPOLY_DEG * W + s];
+    for (int s = 1; s < W; ++s) out[s] = c[WPOLY_DEG * WP + s];
 #pragma unroll
     for (int k = WPOLY_DEG - 1; k >= 0; --k) {
 #pragma unroll
-        for (int s = 1; s < W; ++s) out[s] = fmaf(out[s], v, c[k * W + s]);
+        for (int s = 1; s < W; ++s) out[s] = fmaf(out[s], v, c[k * WP + s]);
     }
     out[0] = (u == 0.f) ? 1.f : 0.f;
+}
+
+// the taps of two coordinates at once, each coefficient row read with 16-byte loads
+// (c must be 16-byte aligned)
+template <int W>
+__device__ __forceinline__ void poly_taps2(const float* __restrict__ c, float u0, float u1, float* o0, float* o1) {
+    constexpr int WP = wpoly_stride(W);
+    const float v0 = 2.f * u0 - 1.f, v1 = 2.f * u1 - 1.f;
+    float a0[WP], a1[WP];
+#pragma unroll
+    for (int q = 0; q < WP / 4; ++q) {
+        const float4 t = reinterpret_cast<const float4*>(c + WPOLY_DEG * WP)[q];
+        a0[4 * q] = t.x; a0[4 * q + 1] = t.y; a0[4 * q + 2] = t.z; a0[4 * q + 3] = t.w;
+        a1[4 * q] = t.x; a1[4 * q + 1] = t.y; a1[4 * q + 2] = t.z; a1[4 * q + 3] = t.w;
+    }
+#pragma unroll
+    for (int k = WPOLY_DEG - 1; k >= 0; --k) {
+#pragma unroll
+        for (int q = 0; q < WP / 4; ++q) {
+            const float4 t = reinterpret_cast<const float4*>(c + k * WP)[q];
+            a0[4 * q] = fmaf(a0[4 * q], v0, t.x); a1[4 * q] = fmaf(a1[4 * q], v1, t.x);
+            a0[4 * q + 1] = fmaf(a0[4 * q + 1], v0, t.y); a1[4 * q + 1] = fmaf(a1[4 * q + 1], v1, t.y);
+            a0[4 * q + 2] = fmaf(a0[4 * q + 2], v0, t.z); a1[4 * q + 2] = fmaf(a1[4 * q + 2], v1, t.z);
+            a0[4 * q + 3] = fmaf(a0[4 * q + 3], v0, t.w); a1[4 * q + 3] = fmaf(a1[4 * q + 3], v1, t.w);
+        }
+    }
+#pragma unroll
+    for (int s = 1; s < W; ++s) { o0[s] = a0[s]; o1[s] = a1[s]; }
+    o0[0] = (u0 == 0.f) ? 1.f : 0.f;
+    o1[0] = (u1 == 0.f) ? 1.f : 0.f;
 }
 
 // ----------------------------------------------------------------------------------------

@@ -135,10 +135,10 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
     R* psx = reinterpret_cast<R*>(cy + 32 * WE);            // [32][WE] psi_x
     int* meta = reinterpret_cast<int*>(psx + 32 * WE);      // [32][3]  oy, ox, sorted index
     cx<R>* cst = reinterpret_cast<cx<R>*>(meta + 96);       // [32]     c_j (B_opt mode)
-    float* poly = reinterpret_cast<float*>(cst + 32);       // [(WPOLY_DEG+1) * W] window polynomial
+    float* poly = reinterpret_cast<float*>(cst + 32);       // [(WPOLY_DEG+1) * WP] window polynomial (16-byte rows)
     const bool use_poly = F32 && !BOPT && J.wpoly != nullptr;
     if (use_poly) {
-        for (int e = lane; e < (WPOLY_DEG + 1) * W; e += 32) poly[e] = J.wpoly[e];
+        for (int e = lane; e < (WPOLY_DEG + 1) * wpoly_stride(W); e += 32) poly[e] = J.wpoly[e];
     }
 
     const int ty = item.x / J.ntile, tx = item.x % J.ntile;
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
             cx<R> fv = J.in[j];
             if (J.mode == INFFT_MODE_DCF) fv = mul(J.w[i], fv);
             const uint32_t cl = __ldg(J.cell + i);
-            const int cxl = (int)(cl % (uint32_t)Ms), cyl = (int)(cl / (uint32_t)Ms);
+            const int cxl = (int)(cl & (uint32_t)(Ms - 1)), cyl = (int)(cl >> (31 - __clz(Ms)));
             meta[lane * 3 + 0] = cyl - ty * T;
             meta[lane * 3 + 1] = cxl - tx * T;
             meta[lane * 3 + 2] = i;
@@ -170,8 +170,7 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
                 bool done = false;
                 if constexpr (F32) {
                     if (use_poly) {
-                        poly_taps<W>(poly, uy, wy);
-                        poly_taps<W>(poly, ux, wx);
+                        poly_taps2<W>(poly, uy, ux, wy, wx);
                         done = true;
                     }
                 }
@@ -605,7 +604,7 @@ static infft_status launch_spread2d_m(JobSet<R>& js, cudaStream_t st) {
     constexpr int W = 2 * MM + 1;
     constexpr int WE = W + 1;
     size_t spw = 32 * WE * sizeof(cx<R>) + 32 * WE * sizeof(R) + 96 * sizeof(int) + 32 * sizeof(cx<R>) +
-                 (WPOLY_DEG + 1) * W * sizeof(float);
+                 (WPOLY_DEG + 1) * wpoly_stride(W) * sizeof(float);
     spw = (spw + 15) & ~(size_t)15;
     js.smem_per_warp = (int)spw;
     js.wpb = 4;

@@ -210,10 +210,11 @@ __global__ void k_tables(int M, int Ms, int m, int window, double beta, R* __res
 __global__ void k_wpoly(int m, double beta, float* __restrict__ coef) {
     constexpr int P1 = WPOLY_DEG + 1;
     const int W = 2 * m + 1;
+    const int WP = wpoly_stride(W);
     const int s = threadIdx.x;
-    if (s >= W) return;
-    if (s == 0) {
-        for (int k = 0; k < P1; ++k) coef[k * W] = 0.f;
+    if (s >= WP) return;
+    if (s == 0 || s >= W) {  // tap 0 keeps the exact rule; padding slots are zero
+        for (int k = 0; k < P1; ++k) coef[k * WP + s] = 0.f;
         return;
     }
     double fv[P1], c[P1], a[P1], tp[P1], tc[P1], tn[P1];
@@ -237,7 +238,7 @@ __global__ void k_wpoly(int m, double beta, float* __restrict__ coef) {
         for (int k = 0; k < P1; ++k) tn[k] = -tp[k] + ((k > 0) ? 2.0 * tc[k - 1] : 0.0);
         for (int k = 0; k < P1; ++k) { a[k] += c[j] * tn[k]; tp[k] = tc[k]; tc[k] = tn[k]; }
     }
-    for (int k = 0; k < P1; ++k) coef[k * W + s] = (float)a[k];
+    for (int k = 0; k < P1; ++k) coef[k * WP + s] = (float)a[k];
 }
 
 // ----------------------------------------------------------------------------------------
@@ -383,7 +384,7 @@ static infft_status build_plan(infft_plan_s* p, const double* x_in, cudaStream_t
 
     // window polynomials (float32 Kaiser-Bessel plans)
     if (!p->fp64 && p->window == WK_KB && 2 * m + 1 <= 32) {
-        INFFT_TRY(dev_alloc(p, (void**)&p->wpoly, (size_t)(WPOLY_DEG + 1) * (2 * m + 1) * sizeof(float)));
+        INFFT_TRY(dev_alloc(p, (void**)&p->wpoly, (size_t)(WPOLY_DEG + 1) * wpoly_stride(2 * m + 1) * sizeof(float)));
         k_wpoly<<<1, 32, 0, st>>>(m, p->beta, p->wpoly);
         INFFT_LAUNCHED();
     }
