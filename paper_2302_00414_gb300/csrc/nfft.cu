@@ -109,21 +109,16 @@ __global__ void __launch_bounds__(128) k_spread(const __grid_constant__ JobSet<R
 // item; lane l owns column l of the item's P x P padded tile (P = T + 2m + 1 <= 32).
 // The item's points are sorted by base row, so the rows a point can touch,
 // [oy, oy + 2m] (padded coordinates; one more row for B_opt slots), only move down:
-// each lane keeps those rows of its column in registers, adds the point's taps, and
-// when the next point starts lower it stores the rows that no later point can reach.
-// Every padded cell is stored exactly once: no shared-memory read-modify-write, no
-// atomics, fixed summation order.
-// Points are staged 32 at a time: each lane evaluates the window of one point and
-// writes the point's row coefficients c_j psi_y[k] and its weight for every lane
-// (psi_x at that lane's column, 0 elsewhere).  The accumulation loop then needs three
-// independent shared-memory loads per point, fetched one point ahead, and the next
-// chunk's point data is loaded from global memory while the current chunk is added.
+// each lane keeps those rows of its column in registers, adds the point's taps
+// (coefficient c_j psi_y[k] broadcast, times psi_x of its column), and when the next
+// point starts lower it stores the rows that no later point can reach.  Every padded
+// cell is stored exactly once, no shared-memory read-modify-write, no atomics.
+// Window values are computed once per point while staging 32 points per warp.
 template <class R, int MM, bool BOPT>
 __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet<R> js) {
     constexpr int W = 2 * MM + 1;              // window taps per axis
     constexpr int WE = W + 1;                  // even stride of the staged rows (16-byte loads)
     constexpr int WR = BOPT ? W + 1 : W;       // rows held in registers
-    constexpr int XS = 33;                     // stride of the lane-weight rows (no bank conflicts)
     constexpr bool F32 = sizeof(R) == 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -134,16 +129,13 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
     const int it = gitem - js.pre_items[jb];
     const int4 item = J.items[it];
     const int P = J.P, Ms = J.Ms, T = J.T;
-    const int logMs = 31 - __clz(Ms);
 
     unsigned char* base = smem_raw + (size_t)warp * js.smem_per_warp;
-    cx<R>* cy = reinterpret_cast<cx<R>*>(base);            // [32][WE] c_j psi_y[k]
-    R* wxr = reinterpret_cast<R*>(cy + 32 * WE);            // [32][XS] weight of each lane's column
-    int* oyv = reinterpret_cast<int*>(wxr + 32 * XS);       // [32] base row (padded coordinates)
-    int* oxv = oyv + 32;                                    // [32] base column (B_opt)
-    int* idv = oxv + 32;                                    // [32] sorted index (B_opt)
-    cx<R>* cst = reinterpret_cast<cx<R>*>(idv + 32);        // [32] c_j (B_opt)
-    float* poly = reinterpret_cast<float*>(cst + 32);       // window polynomial (16-byte rows)
+    cx<R>* cy = reinterpret_cast<cx<R>*>(base);            // [32][WE] c_j psi_y (window mode)
+    R* psx = reinterpret_cast<R*>(cy + 32 * WE);            // [32][WE] psi_x
+    int* meta = reinterpret_cast<int*>(psx + 32 * WE);      // [32][3]  oy, ox, sorted index
+    cx<R>* cst = reinterpret_cast<cx<R>*>(meta + 96);       // [32]     c_j (B_opt mode)
+    float* poly = reinterpret_cast<float*>(cst + 32);       // [(WPOLY_DEG+1) * WP] window polynomial (16-byte rows)
     const bool use_poly = F32 && !BOPT && J.wpoly != nullptr;
     if (use_poly) {
         for (int e = lane; e < (WPOLY_DEG + 1) * wpoly_stride(W); e += 32) poly[e] = J.wpoly[e];
@@ -156,46 +148,24 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
     int r0 = 0;  // padded row held in are[0]
     cx<R>* dst = J.padded + (size_t)it * P * P;
     const bool col_ok = lane < P;
-    const bool dcf = J.mode == INFFT_MODE_DCF;
-
-    // raw point data of the next chunk, loaded ahead
-    int j_n = 0;
-    uint32_t cl_n = 0;
-    R uy_n = R(0), ux_n = R(0);
-    cx<R> w_n = mk<R>(R(1), R(0));
-    auto fetch = [&](int c0) {
-        if (c0 + lane < item.z) {
-            const int i = item.y + c0 + lane;
-            j_n = __ldg(J.perm + i);
-            cl_n = __ldg(J.cell + i);
-            if (!BOPT) {
-                uy_n = J.u[(size_t)i * 2 + 0];
-                ux_n = J.u[(size_t)i * 2 + 1];
-            }
-            if (dcf) w_n = J.w[i];
-        }
-    };
-    fetch(0);
 
     for (int c0 = 0; c0 < item.z; c0 += 32) {
         const int np = min(32, item.z - c0);
-        // stage this chunk from the prefetched data
-        const int j = j_n;
-        const uint32_t cl = cl_n;
-        const R uy = uy_n, ux = ux_n;
-        const cx<R> wv = w_n;
         __syncwarp();
         if (lane < np) {
+            const int i = item.y + c0 + lane;
+            const int j = __ldg(J.perm + i);
             cx<R> fv = J.in[j];
-            if (dcf) fv = mul(wv, fv);
-            const int oy = (int)(cl >> logMs) - ty * T;
-            const int ox = (int)(cl & (uint32_t)(Ms - 1)) - tx * T;
-            oyv[lane] = oy;
+            if (J.mode == INFFT_MODE_DCF) fv = mul(J.w[i], fv);
+            const uint32_t cl = __ldg(J.cell + i);
+            const int cxl = (int)(cl & (uint32_t)(Ms - 1)), cyl = (int)(cl >> (31 - __clz(Ms)));
+            meta[lane * 3 + 0] = cyl - ty * T;
+            meta[lane * 3 + 1] = cxl - tx * T;
+            meta[lane * 3 + 2] = i;
             if (BOPT) {
-                oxv[lane] = ox;
-                idv[lane] = item.y + c0 + lane;
                 cst[lane] = fv;
             } else {
+                const R uy = J.u[(size_t)i * 2 + 0], ux = J.u[(size_t)i * 2 + 1];
                 R wy[W], wx[W];
                 bool done = false;
                 if constexpr (F32) {
@@ -212,34 +182,32 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
                     }
                 }
 #pragma unroll
-                for (int s = 0; s < W; ++s) cy[lane * WE + s] = scale(fv, wy[s]);
+                for (int s = 0; s < W; ++s) {
+                    cy[lane * WE + s] = scale(fv, wy[s]);
+                    psx[lane * WE + s] = wx[s];
+                }
                 cy[lane * WE + W] = mk<R>(0, 0);
-                R* row = wxr + lane * XS;
-#pragma unroll
-                for (int q = 0; q < 32; ++q) row[q] = R(0);
-#pragma unroll
-                for (int s = 0; s < W; ++s) row[ox + s] = wx[s];   // ox + s <= T - 1 + 2m < 32
             }
         }
         __syncwarp();
-        fetch(c0 + 32);  // overlaps the accumulation below
-
-        if (BOPT) {
-            constexpr int S = W + 1;
-            for (int p = 0; p < np; ++p) {
-                const int oy = oyv[p];
-                while (r0 < oy) {
-                    if (col_ok) dst[(size_t)r0 * P + lane] = mk<R>(are[0], aim[0]);
+        for (int p = 0; p < np; ++p) {
+            const int oy = meta[p * 3 + 0], ox = meta[p * 3 + 1];
+            // store the rows above oy: no later point reaches them
+            while (r0 < oy) {
+                if (col_ok) dst[(size_t)r0 * P + lane] = mk<R>(are[0], aim[0]);
 #pragma unroll
-                    for (int k = 0; k < WR - 1; ++k) { are[k] = are[k + 1]; aim[k] = aim[k + 1]; }
-                    are[WR - 1] = R(0);
-                    aim[WR - 1] = R(0);
-                    ++r0;
-                }
-                const int sx = lane - oxv[p];
+                for (int k = 0; k < WR - 1; ++k) { are[k] = are[k + 1]; aim[k] = aim[k + 1]; }
+                are[WR - 1] = R(0);
+                aim[WR - 1] = R(0);
+                ++r0;
+            }
+            const int sx = lane - ox;
+            if (BOPT) {
+                constexpr int S = W + 1;
                 if (sx >= 0 && sx < S) {
+                    const int i = meta[p * 3 + 2];
                     const cx<R> cv = cst[p];
-                    const cx<R>* cf = J.coef + (size_t)idv[p] * S * S + sx;
+                    const cx<R>* cf = J.coef + (size_t)i * S * S + sx;
 #pragma unroll
                     for (int k = 0; k < S; ++k) {
                         const cx<R> b = cf[k * S];
@@ -247,69 +215,30 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
                         aim[k] += b.re * cv.im - b.im * cv.re;
                     }
                 }
-            }
-        } else if constexpr (F32) {
-            constexpr int NQ = WE / 2;
-            int oy_n = oyv[0];
-            float wx_n = wxr[lane];
-            float4 c_n[NQ];
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) c_n[q] = reinterpret_cast<const float4*>(cy)[q];
-            for (int p = 0; p < np; ++p) {
-                const int oy = oy_n;
-                const float wxv = wx_n;
-                float4 c[NQ];
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) c[q] = c_n[q];
-                if (p + 1 < np) {
-                    oy_n = oyv[p + 1];
-                    wx_n = wxr[(p + 1) * XS + lane];
-                    const float4* cn = reinterpret_cast<const float4*>(cy + (p + 1) * WE);
-#pragma unroll
-                    for (int q = 0; q < NQ; ++q) c_n[q] = cn[q];
-                }
-                while (r0 < oy) {
-                    if (col_ok) dst[(size_t)r0 * P + lane] = mk<R>(are[0], aim[0]);
-#pragma unroll
-                    for (int k = 0; k < WR - 1; ++k) { are[k] = are[k + 1]; aim[k] = aim[k + 1]; }
-                    are[WR - 1] = R(0);
-                    aim[WR - 1] = R(0);
-                    ++r0;
-                }
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) {
-                    are[2 * q] += c[q].x * wxv;
-                    aim[2 * q] += c[q].y * wxv;
-                    if (2 * q + 1 < W) {
-                        are[2 * q + 1] += c[q].z * wxv;
-                        aim[2 * q + 1] += c[q].w * wxv;
-                    }
-                }
-            }
-        } else {
-            int oy_n = oyv[0];
-            R wx_n = wxr[lane];
-            for (int p = 0; p < np; ++p) {
-                const int oy = oy_n;
-                const R wxv = wx_n;
-                if (p + 1 < np) {
-                    oy_n = oyv[p + 1];
-                    wx_n = wxr[(p + 1) * XS + lane];
-                }
-                while (r0 < oy) {
-                    if (col_ok) dst[(size_t)r0 * P + lane] = mk<R>(are[0], aim[0]);
-#pragma unroll
-                    for (int k = 0; k < WR - 1; ++k) { are[k] = are[k + 1]; aim[k] = aim[k + 1]; }
-                    are[WR - 1] = R(0);
-                    aim[WR - 1] = R(0);
-                    ++r0;
-                }
+            } else {
+                const bool in = (sx >= 0) && (sx < W);
+                const R wx = in ? psx[p * WE + (in ? sx : 0)] : R(0);
                 const cx<R>* cp = cy + p * WE;
+                if constexpr (F32) {
+                    // two complex coefficients per 16-byte broadcast load
+                    const float4* cp4 = reinterpret_cast<const float4*>(cp);
 #pragma unroll
-                for (int k = 0; k < W; ++k) {
-                    const cx<R> c = cp[k];
-                    are[k] += c.re * wxv;
-                    aim[k] += c.im * wxv;
+                    for (int k2 = 0; k2 < WE / 2; ++k2) {
+                        const float4 c = cp4[k2];
+                        are[2 * k2] += c.x * wx;
+                        aim[2 * k2] += c.y * wx;
+                        if (2 * k2 + 1 < W) {
+                            are[2 * k2 + 1] += c.z * wx;
+                            aim[2 * k2 + 1] += c.w * wx;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < W; ++k) {
+                        const cx<R> c = cp[k];
+                        are[k] += c.re * wx;
+                        aim[k] += c.im * wx;
+                    }
                 }
             }
         }
@@ -323,6 +252,182 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
         aim[WR - 1] = R(0);
         ++r0;
     }
+}
+
+// ---------------------------------------------------------------------------------------
+// Paired two-dimensional spreading (window mode, T = 16, m <= 4).  The padded columns a
+// point can touch, [ox, ox + 2m], lie inside [0, 16) when ox < 16 - 2m and inside
+// [T + 2m - 16, T + 2m) otherwise.  Lanes 0..15 own columns 0..15 and lanes 16..31 own
+// columns T + 2m - 16 .. T + 2m - 1, so two points of the same base row -- one from
+// each side -- are added in the same instructions.  The columns both halves own are
+// summed with one shuffle when a row is stored.  Pairs are formed per row within each
+// staged chunk of 32 points with warp ballots; unpaired points run with half the warp.
+template <class R, int MM>
+__global__ void __launch_bounds__(128) k_spread2d_pair(const __grid_constant__ JobSet<R> js) {
+    constexpr int W = 2 * MM + 1;
+    constexpr int WE = W + 1;
+    constexpr int TT = 16;                        // tile edge this kernel requires
+    constexpr int SPLIT = 16 - 2 * MM;            // ox < SPLIT: left half
+    constexpr int OFF = TT + 2 * MM - 16;         // first column owned by the right half
+    constexpr bool F32 = sizeof(R) == 4;
+    static_assert(TT + 4 * MM <= 32, "windows must fit in a half-warp");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gitem = blockIdx.x * js.wpb + warp;
+    if (gitem >= js.pre_items[js.njobs]) return;
+    const int jb = find_job(js.pre_items, js.njobs, gitem);
+    const Job<R>& J = js.job[jb];
+    const int it = gitem - js.pre_items[jb];
+    const int4 item = J.items[it];
+    const int P = J.P, Ms = J.Ms;
+
+    unsigned char* base = smem_raw + (size_t)warp * js.smem_per_warp;
+    cx<R>* cy = reinterpret_cast<cx<R>*>(base);            // [32][WE] c_j psi_y
+    R* psx = reinterpret_cast<R*>(cy + 32 * WE);            // [32][WE] psi_x
+    int* meta = reinterpret_cast<int*>(psx + 32 * WE);      // [32][2]  oy, ox
+    int2* sched = reinterpret_cast<int2*>(meta + 64);       // [32]     (left, right) pairs
+    float* poly = reinterpret_cast<float*>(sched + 32);     // window polynomial (16-byte rows)
+    const bool use_poly = F32 && J.wpoly != nullptr;
+    if (use_poly) {
+        for (int e = lane; e < (WPOLY_DEG + 1) * wpoly_stride(W); e += 32) poly[e] = J.wpoly[e];
+    }
+
+    const int ty = item.x / J.ntile, tx = item.x % J.ntile;
+    const bool right = lane >= 16;
+    const int col = right ? lane - 16 + OFF : lane;
+    R are[W], aim[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) { are[k] = R(0); aim[k] = R(0); }
+    int r0 = 0;
+    cx<R>* dst = J.padded + (size_t)it * P * P;
+    const unsigned lt = (1u << lane) - 1u;
+
+    // store padded row r0 (both halves' shares of the shared columns summed) and shift
+    auto flush_row = [&]() {
+        // the right lane owning the same column as left lane c (c >= OFF) is c + 16 - OFF
+        const R pre = __shfl_down_sync(0xffffffffu, are[0], 16 - OFF);
+        const R pim = __shfl_down_sync(0xffffffffu, aim[0], 16 - OFF);
+        R vre = are[0], vim = aim[0];
+        if (!right && col >= OFF) { vre += pre; vim += pim; }
+        cx<R>* rowp = dst + (size_t)r0 * P;
+        if (!right) rowp[col] = mk<R>(vre, vim);
+        else if (col >= 16) rowp[col] = mk<R>(vre, vim);
+        else if (lane == 16) rowp[TT + 2 * MM] = mk<R>(R(0), R(0));  // last column (B_opt slot) is empty
+#pragma unroll
+        for (int k = 0; k < W - 1; ++k) { are[k] = are[k + 1]; aim[k] = aim[k + 1]; }
+        are[W - 1] = R(0);
+        aim[W - 1] = R(0);
+        ++r0;
+    };
+
+    for (int c0 = 0; c0 < item.z; c0 += 32) {
+        const int np = min(32, item.z - c0);
+        __syncwarp();
+        int oy = 0x7fffffff, ox = 0;
+        bool isR = false;
+        if (lane < np) {
+            const int i = item.y + c0 + lane;
+            const int j = __ldg(J.perm + i);
+            cx<R> fv = J.in[j];
+            if (J.mode == INFFT_MODE_DCF) fv = mul(J.w[i], fv);
+            const uint32_t cl = __ldg(J.cell + i);
+            oy = (int)(cl >> (31 - __clz(Ms))) - ty * TT;
+            ox = (int)(cl & (uint32_t)(Ms - 1)) - tx * TT;
+            isR = ox >= SPLIT;
+            meta[lane * 2 + 0] = oy;
+            meta[lane * 2 + 1] = ox;
+            const R uy = J.u[(size_t)i * 2 + 0], ux = J.u[(size_t)i * 2 + 1];
+            R wy[W], wx[W];
+            bool done = false;
+            if constexpr (F32) {
+                if (use_poly) {
+                    poly_taps2<W>(poly, uy, ux, wy, wx);
+                    done = true;
+                }
+            }
+            if (!done) {
+#pragma unroll
+                for (int s = 0; s < W; ++s) {
+                    wy[s] = tap_weight<R>(J.window, uy, s, MM, J.inv_m, J.beta);
+                    wx[s] = tap_weight<R>(J.window, ux, s, MM, J.inv_m, J.beta);
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < W; ++s) {
+                cy[lane * WE + s] = scale(fv, wy[s]);
+                psx[lane * WE + s] = wx[s];
+            }
+            cy[lane * WE + W] = mk<R>(0, 0);
+        }
+        // pairing schedule: rows (segments of equal oy) in order; within a row the left
+        // points (sorted by ox, so a prefix) pair with the right points by rank
+        const int prev_oy = __shfl_up_sync(0xffffffffu, oy, 1);
+        const bool valid = lane < np;
+        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+        const unsigned starts = __ballot_sync(0xffffffffu, valid && (lane == 0 || oy != prev_oy));
+        const unsigned rmask = __ballot_sync(0xffffffffu, valid && isR);
+        const unsigned lmask = vmask & ~rmask;
+        const int seg_start = 31 - __clz(starts & (lt | (1u << lane)));
+        const unsigned after = starts & ~(lt | (1u << lane));
+        const int seg_end = after ? __ffs(after) - 1 : np;   // exclusive
+        const unsigned segmask = (seg_end >= 32 ? 0xffffffffu : ((1u << seg_end) - 1u)) & ~((1u << seg_start) - 1u);
+        const int nL = __popc(lmask & segmask), nR = __popc(rmask & segmask);
+        const int nslot = max(nL, nR);
+        // exclusive prefix of slot counts over segment starts
+        int sc = (valid && lane == seg_start) ? nslot : 0;
+        int incl = sc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int seg_base = __shfl_sync(0xffffffffu, incl - sc, seg_start);
+        const int total_slots = __shfl_sync(0xffffffffu, incl, 31);
+        if (lane < total_slots) sched[lane] = make_int2(-1, -1);
+        __syncwarp();
+        if (valid) {
+            const int rank = __popc((isR ? rmask : lmask) & segmask & lt);
+            int* slot = reinterpret_cast<int*>(sched + seg_base + rank);
+            slot[isR ? 1 : 0] = lane;
+        }
+        __syncwarp();
+        for (int k = 0; k < total_slots; ++k) {
+            const int2 pr = sched[k];
+            const int head = pr.x >= 0 ? pr.x : pr.y;
+            const int rowy = meta[head * 2];
+            while (r0 < rowy) flush_row();
+            const int mp = right ? pr.y : pr.x;
+            R wxv = R(0);
+            int src = 0;
+            if (mp >= 0) {
+                const int sx = col - meta[mp * 2 + 1];
+                if (sx >= 0 && sx < W) wxv = psx[mp * WE + sx];
+                src = mp;
+            }
+            const cx<R>* cp = cy + src * WE;
+            if constexpr (F32) {
+                const float4* cp4 = reinterpret_cast<const float4*>(cp);
+#pragma unroll
+                for (int k2 = 0; k2 < WE / 2; ++k2) {
+                    const float4 c = cp4[k2];
+                    are[2 * k2] += c.x * wxv;
+                    aim[2 * k2] += c.y * wxv;
+                    if (2 * k2 + 1 < W) {
+                        are[2 * k2 + 1] += c.z * wxv;
+                        aim[2 * k2 + 1] += c.w * wxv;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int kk = 0; kk < W; ++kk) {
+                    const cx<R> c = cp[kk];
+                    are[kk] += c.re * wxv;
+                    aim[kk] += c.im * wxv;
+                }
+            }
+        }
+    }
+    while (r0 < P) flush_row();
 }
 
 template <class R, int D>
@@ -674,7 +779,7 @@ template <class R, int MM, bool BOPT>
 static infft_status launch_spread2d_m(JobSet<R>& js, cudaStream_t st) {
     constexpr int W = 2 * MM + 1;
     constexpr int WE = W + 1;
-    size_t spw = 32 * WE * sizeof(cx<R>) + 32 * 33 * sizeof(R) + 96 * sizeof(int) + 32 * sizeof(cx<R>) +
+    size_t spw = 32 * WE * sizeof(cx<R>) + 32 * WE * sizeof(R) + 96 * sizeof(int) + 32 * sizeof(cx<R>) +
                  (WPOLY_DEG + 1) * wpoly_stride(W) * sizeof(float);
     spw = (spw + 15) & ~(size_t)15;
     js.smem_per_warp = (int)spw;
@@ -688,8 +793,37 @@ static infft_status launch_spread2d_m(JobSet<R>& js, cudaStream_t st) {
     return INFFT_OK;
 }
 
+template <class R, int MM>
+static infft_status launch_spread2d_pair_m(JobSet<R>& js, cudaStream_t st) {
+    constexpr int W = 2 * MM + 1;
+    constexpr int WE = W + 1;
+    size_t spw = 32 * WE * sizeof(cx<R>) + 32 * WE * sizeof(R) + 64 * sizeof(int) + 32 * sizeof(int2) +
+                 (WPOLY_DEG + 1) * wpoly_stride(W) * sizeof(float);
+    spw = (spw + 15) & ~(size_t)15;
+    js.smem_per_warp = (int)spw;
+    js.wpb = 4;
+    const int nitems = js.pre_items[js.njobs];
+    if (nitems == 0) return INFFT_OK;
+    const size_t smem = spw * js.wpb;
+    INFFT_CUDA(cudaFuncSetAttribute(k_spread2d_pair<R, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_spread2d_pair<R, MM><<<(nitems + js.wpb - 1) / js.wpb, 32 * js.wpb, smem, st>>>(js);
+    INFFT_LAUNCHED();
+    return INFFT_OK;
+}
+
 template <class R, bool BOPT>
 static infft_status launch_spread2d(JobSet<R>& js, cudaStream_t st, int m) {
+    if (!BOPT && m >= 2 && m <= 4) {
+        bool t16 = true;
+        for (int j = 0; j < js.njobs; ++j) t16 = t16 && js.job[j].T == 16;
+        if (t16) {
+            switch (m) {
+                case 2: return launch_spread2d_pair_m<R, 2>(js, st);
+                case 3: return launch_spread2d_pair_m<R, 3>(js, st);
+                default: return launch_spread2d_pair_m<R, 4>(js, st);
+            }
+        }
+    }
     switch (m) {
         case 2: return launch_spread2d_m<R, 2, BOPT>(js, st);
         case 3: return launch_spread2d_m<R, 3, BOPT>(js, st);
