@@ -126,27 +126,28 @@ __device__ __forceinline__ void poly_taps(const float* __restrict__ c, float u, 
 template <int W>
 __device__ __forceinline__ void poly_taps2(const float* __restrict__ c, float u0, float u1, float* o0, float* o1) {
     constexpr int WP = wpoly_stride(W);
-    const float v0 = 2.f * u0 - 1.f, v1 = 2.f * u1 - 1.f;
-    float a0[WP], a1[WP];
+    // Horner on both coordinates at once: one packed two-wide FMA per tap and degree
+    const float2 vv = make_float2(2.f * u0 - 1.f, 2.f * u1 - 1.f);
+    float2 a[WP];
 #pragma unroll
     for (int q = 0; q < WP / 4; ++q) {
         const float4 t = reinterpret_cast<const float4*>(c + WPOLY_DEG * WP)[q];
-        a0[4 * q] = t.x; a0[4 * q + 1] = t.y; a0[4 * q + 2] = t.z; a0[4 * q + 3] = t.w;
-        a1[4 * q] = t.x; a1[4 * q + 1] = t.y; a1[4 * q + 2] = t.z; a1[4 * q + 3] = t.w;
+        a[4 * q] = make_float2(t.x, t.x); a[4 * q + 1] = make_float2(t.y, t.y);
+        a[4 * q + 2] = make_float2(t.z, t.z); a[4 * q + 3] = make_float2(t.w, t.w);
     }
 #pragma unroll
     for (int k = WPOLY_DEG - 1; k >= 0; --k) {
 #pragma unroll
         for (int q = 0; q < WP / 4; ++q) {
             const float4 t = reinterpret_cast<const float4*>(c + k * WP)[q];
-            a0[4 * q] = fmaf(a0[4 * q], v0, t.x); a1[4 * q] = fmaf(a1[4 * q], v1, t.x);
-            a0[4 * q + 1] = fmaf(a0[4 * q + 1], v0, t.y); a1[4 * q + 1] = fmaf(a1[4 * q + 1], v1, t.y);
-            a0[4 * q + 2] = fmaf(a0[4 * q + 2], v0, t.z); a1[4 * q + 2] = fmaf(a1[4 * q + 2], v1, t.z);
-            a0[4 * q + 3] = fmaf(a0[4 * q + 3], v0, t.w); a1[4 * q + 3] = fmaf(a1[4 * q + 3], v1, t.w);
+            if (4 * q < W) a[4 * q] = __ffma2_rn(a[4 * q], vv, make_float2(t.x, t.x));
+            if (4 * q + 1 < W) a[4 * q + 1] = __ffma2_rn(a[4 * q + 1], vv, make_float2(t.y, t.y));
+            if (4 * q + 2 < W) a[4 * q + 2] = __ffma2_rn(a[4 * q + 2], vv, make_float2(t.z, t.z));
+            if (4 * q + 3 < W) a[4 * q + 3] = __ffma2_rn(a[4 * q + 3], vv, make_float2(t.w, t.w));
         }
     }
 #pragma unroll
-    for (int s = 1; s < W; ++s) { o0[s] = a0[s]; o1[s] = a1[s]; }
+    for (int s = 1; s < W; ++s) { o0[s] = a[s].x; o1[s] = a[s].y; }
     o0[0] = (u0 == 0.f) ? 1.f : 0.f;
     o1[0] = (u1 == 0.f) ? 1.f : 0.f;
 }

@@ -4,6 +4,7 @@
 // inverse FFT passes (Algorithm 2.1 steps 1-2) and tile-sorted interpolation
 // (Algorithm 2.1 step 3).
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -142,12 +143,14 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
     }
 
     const int ty = item.x / J.ntile, tx = item.x % J.ntile;
-    R are[WR], aim[WR];
+    using V2 = typename std::conditional<F32, float2, double2>::type;
+    V2 acc[WR];  // (re, im) of the rows r0 .. r0 + WR - 1 of this lane's column
 #pragma unroll
-    for (int k = 0; k < WR; ++k) { are[k] = R(0); aim[k] = R(0); }
-    int r0 = 0;  // padded row held in are[0]
+    for (int k = 0; k < WR; ++k) { acc[k].x = R(0); acc[k].y = R(0); }
+    int r0 = 0;  // padded row held in acc[0]
     cx<R>* dst = J.padded + (size_t)it * P * P;
     const bool col_ok = lane < P;
+    const int logMs = 31 - __clz(Ms);
 
     for (int c0 = 0; c0 < item.z; c0 += 32) {
         const int np = min(32, item.z - c0);
@@ -158,7 +161,7 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
             cx<R> fv = J.in[j];
             if (J.mode == INFFT_MODE_DCF) fv = mul(J.w[i], fv);
             const uint32_t cl = __ldg(J.cell + i);
-            const int cxl = (int)(cl & (uint32_t)(Ms - 1)), cyl = (int)(cl >> (31 - __clz(Ms)));
+            const int cxl = (int)(cl & (uint32_t)(Ms - 1)), cyl = (int)(cl >> logMs);
             meta[lane * 3 + 0] = cyl - ty * T;
             meta[lane * 3 + 1] = cxl - tx * T;
             meta[lane * 3 + 2] = i;
@@ -194,11 +197,11 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
             const int oy = meta[p * 3 + 0], ox = meta[p * 3 + 1];
             // store the rows above oy: no later point reaches them
             while (r0 < oy) {
-                if (col_ok) dst[(size_t)r0 * P + lane] = mk<R>(are[0], aim[0]);
+                if (col_ok) dst[(size_t)r0 * P + lane] = mk<R>(acc[0].x, acc[0].y);
 #pragma unroll
-                for (int k = 0; k < WR - 1; ++k) { are[k] = are[k + 1]; aim[k] = aim[k + 1]; }
-                are[WR - 1] = R(0);
-                aim[WR - 1] = R(0);
+                for (int k = 0; k < WR - 1; ++k) acc[k] = acc[k + 1];
+                acc[WR - 1].x = R(0);
+                acc[WR - 1].y = R(0);
                 ++r0;
             }
             const int sx = lane - ox;
@@ -211,8 +214,8 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
 #pragma unroll
                     for (int k = 0; k < S; ++k) {
                         const cx<R> b = cf[k * S];
-                        are[k] += b.re * cv.re + b.im * cv.im;   // conj(b) f
-                        aim[k] += b.re * cv.im - b.im * cv.re;
+                        acc[k].x += b.re * cv.re + b.im * cv.im;   // conj(b) f
+                        acc[k].y += b.re * cv.im - b.im * cv.re;
                     }
                 }
             } else {
@@ -220,24 +223,22 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
                 const R wx = in ? psx[p * WE + (in ? sx : 0)] : R(0);
                 const cx<R>* cp = cy + p * WE;
                 if constexpr (F32) {
-                    // two complex coefficients per 16-byte broadcast load
+                    // two complex coefficients per 16-byte broadcast load, one packed
+                    // two-wide FMA per row
                     const float4* cp4 = reinterpret_cast<const float4*>(cp);
+                    const float2 ww = make_float2(wx, wx);
 #pragma unroll
                     for (int k2 = 0; k2 < WE / 2; ++k2) {
                         const float4 c = cp4[k2];
-                        are[2 * k2] += c.x * wx;
-                        aim[2 * k2] += c.y * wx;
-                        if (2 * k2 + 1 < W) {
-                            are[2 * k2 + 1] += c.z * wx;
-                            aim[2 * k2 + 1] += c.w * wx;
-                        }
+                        acc[2 * k2] = __ffma2_rn(make_float2(c.x, c.y), ww, acc[2 * k2]);
+                        if (2 * k2 + 1 < W) acc[2 * k2 + 1] = __ffma2_rn(make_float2(c.z, c.w), ww, acc[2 * k2 + 1]);
                     }
                 } else {
 #pragma unroll
                     for (int k = 0; k < W; ++k) {
                         const cx<R> c = cp[k];
-                        are[k] += c.re * wx;
-                        aim[k] += c.im * wx;
+                        acc[k].x += c.re * wx;
+                        acc[k].y += c.im * wx;
                     }
                 }
             }
@@ -245,11 +246,11 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
     }
     // remaining rows (including rows no point reached)
     while (r0 < P) {
-        if (col_ok) dst[(size_t)r0 * P + lane] = mk<R>(are[0], aim[0]);
+        if (col_ok) dst[(size_t)r0 * P + lane] = mk<R>(acc[0].x, acc[0].y);
 #pragma unroll
-        for (int k = 0; k < WR - 1; ++k) { are[k] = are[k + 1]; aim[k] = aim[k + 1]; }
-        are[WR - 1] = R(0);
-        aim[WR - 1] = R(0);
+        for (int k = 0; k < WR - 1; ++k) acc[k] = acc[k + 1];
+        acc[WR - 1].x = R(0);
+        acc[WR - 1].y = R(0);
         ++r0;
     }
 }
@@ -813,7 +814,7 @@ static infft_status launch_spread2d_pair_m(JobSet<R>& js, cudaStream_t st) {
 
 template <class R, bool BOPT>
 static infft_status launch_spread2d(JobSet<R>& js, cudaStream_t st, int m) {
-    if (!BOPT && m >= 2 && m <= 4) {
+    if (false) {  // the paired variant is kept for reference but not faster
         bool t16 = true;
         for (int j = 0; j < js.njobs; ++j) t16 = t16 && js.job[j].T == 16;
         if (t16) {
