@@ -255,182 +255,6 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
     }
 }
 
-// ---------------------------------------------------------------------------------------
-// Paired two-dimensional spreading (window mode, T = 16, m <= 4).  The padded columns a
-// point can touch, [ox, ox + 2m], lie inside [0, 16) when ox < 16 - 2m and inside
-// [T + 2m - 16, T + 2m) otherwise.  Lanes 0..15 own columns 0..15 and lanes 16..31 own
-// columns T + 2m - 16 .. T + 2m - 1, so two points of the same base row -- one from
-// each side -- are added in the same instructions.  The columns both halves own are
-// summed with one shuffle when a row is stored.  Pairs are formed per row within each
-// staged chunk of 32 points with warp ballots; unpaired points run with half the warp.
-template <class R, int MM>
-__global__ void __launch_bounds__(128) k_spread2d_pair(const __grid_constant__ JobSet<R> js) {
-    constexpr int W = 2 * MM + 1;
-    constexpr int WE = W + 1;
-    constexpr int TT = 16;                        // tile edge this kernel requires
-    constexpr int SPLIT = 16 - 2 * MM;            // ox < SPLIT: left half
-    constexpr int OFF = TT + 2 * MM - 16;         // first column owned by the right half
-    constexpr bool F32 = sizeof(R) == 4;
-    static_assert(TT + 4 * MM <= 32, "windows must fit in a half-warp");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gitem = blockIdx.x * js.wpb + warp;
-    if (gitem >= js.pre_items[js.njobs]) return;
-    const int jb = find_job(js.pre_items, js.njobs, gitem);
-    const Job<R>& J = js.job[jb];
-    const int it = gitem - js.pre_items[jb];
-    const int4 item = J.items[it];
-    const int P = J.P, Ms = J.Ms;
-
-    unsigned char* base = smem_raw + (size_t)warp * js.smem_per_warp;
-    cx<R>* cy = reinterpret_cast<cx<R>*>(base);            // [32][WE] c_j psi_y
-    R* psx = reinterpret_cast<R*>(cy + 32 * WE);            // [32][WE] psi_x
-    int* meta = reinterpret_cast<int*>(psx + 32 * WE);      // [32][2]  oy, ox
-    int2* sched = reinterpret_cast<int2*>(meta + 64);       // [32]     (left, right) pairs
-    float* poly = reinterpret_cast<float*>(sched + 32);     // window polynomial (16-byte rows)
-    const bool use_poly = F32 && J.wpoly != nullptr;
-    if (use_poly) {
-        for (int e = lane; e < (WPOLY_DEG + 1) * wpoly_stride(W); e += 32) poly[e] = J.wpoly[e];
-    }
-
-    const int ty = item.x / J.ntile, tx = item.x % J.ntile;
-    const bool right = lane >= 16;
-    const int col = right ? lane - 16 + OFF : lane;
-    R are[W], aim[W];
-#pragma unroll
-    for (int k = 0; k < W; ++k) { are[k] = R(0); aim[k] = R(0); }
-    int r0 = 0;
-    cx<R>* dst = J.padded + (size_t)it * P * P;
-    const unsigned lt = (1u << lane) - 1u;
-
-    // store padded row r0 (both halves' shares of the shared columns summed) and shift
-    auto flush_row = [&]() {
-        // the right lane owning the same column as left lane c (c >= OFF) is c + 16 - OFF
-        const R pre = __shfl_down_sync(0xffffffffu, are[0], 16 - OFF);
-        const R pim = __shfl_down_sync(0xffffffffu, aim[0], 16 - OFF);
-        R vre = are[0], vim = aim[0];
-        if (!right && col >= OFF) { vre += pre; vim += pim; }
-        cx<R>* rowp = dst + (size_t)r0 * P;
-        if (!right) rowp[col] = mk<R>(vre, vim);
-        else if (col >= 16) rowp[col] = mk<R>(vre, vim);
-        else if (lane == 16) rowp[TT + 2 * MM] = mk<R>(R(0), R(0));  // last column (B_opt slot) is empty
-#pragma unroll
-        for (int k = 0; k < W - 1; ++k) { are[k] = are[k + 1]; aim[k] = aim[k + 1]; }
-        are[W - 1] = R(0);
-        aim[W - 1] = R(0);
-        ++r0;
-    };
-
-    for (int c0 = 0; c0 < item.z; c0 += 32) {
-        const int np = min(32, item.z - c0);
-        __syncwarp();
-        int oy = 0x7fffffff, ox = 0;
-        bool isR = false;
-        if (lane < np) {
-            const int i = item.y + c0 + lane;
-            const int j = __ldg(J.perm + i);
-            cx<R> fv = J.in[j];
-            if (J.mode == INFFT_MODE_DCF) fv = mul(J.w[i], fv);
-            const uint32_t cl = __ldg(J.cell + i);
-            oy = (int)(cl >> (31 - __clz(Ms))) - ty * TT;
-            ox = (int)(cl & (uint32_t)(Ms - 1)) - tx * TT;
-            isR = ox >= SPLIT;
-            meta[lane * 2 + 0] = oy;
-            meta[lane * 2 + 1] = ox;
-            const R uy = J.u[(size_t)i * 2 + 0], ux = J.u[(size_t)i * 2 + 1];
-            R wy[W], wx[W];
-            bool done = false;
-            if constexpr (F32) {
-                if (use_poly) {
-                    poly_taps2<W>(poly, uy, ux, wy, wx);
-                    done = true;
-                }
-            }
-            if (!done) {
-#pragma unroll
-                for (int s = 0; s < W; ++s) {
-                    wy[s] = tap_weight<R>(J.window, uy, s, MM, J.inv_m, J.beta);
-                    wx[s] = tap_weight<R>(J.window, ux, s, MM, J.inv_m, J.beta);
-                }
-            }
-#pragma unroll
-            for (int s = 0; s < W; ++s) {
-                cy[lane * WE + s] = scale(fv, wy[s]);
-                psx[lane * WE + s] = wx[s];
-            }
-            cy[lane * WE + W] = mk<R>(0, 0);
-        }
-        // pairing schedule: rows (segments of equal oy) in order; within a row the left
-        // points (sorted by ox, so a prefix) pair with the right points by rank
-        const int prev_oy = __shfl_up_sync(0xffffffffu, oy, 1);
-        const bool valid = lane < np;
-        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
-        const unsigned starts = __ballot_sync(0xffffffffu, valid && (lane == 0 || oy != prev_oy));
-        const unsigned rmask = __ballot_sync(0xffffffffu, valid && isR);
-        const unsigned lmask = vmask & ~rmask;
-        const int seg_start = 31 - __clz(starts & (lt | (1u << lane)));
-        const unsigned after = starts & ~(lt | (1u << lane));
-        const int seg_end = after ? __ffs(after) - 1 : np;   // exclusive
-        const unsigned segmask = (seg_end >= 32 ? 0xffffffffu : ((1u << seg_end) - 1u)) & ~((1u << seg_start) - 1u);
-        const int nL = __popc(lmask & segmask), nR = __popc(rmask & segmask);
-        const int nslot = max(nL, nR);
-        // exclusive prefix of slot counts over segment starts
-        int sc = (valid && lane == seg_start) ? nslot : 0;
-        int incl = sc;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const int seg_base = __shfl_sync(0xffffffffu, incl - sc, seg_start);
-        const int total_slots = __shfl_sync(0xffffffffu, incl, 31);
-        if (lane < total_slots) sched[lane] = make_int2(-1, -1);
-        __syncwarp();
-        if (valid) {
-            const int rank = __popc((isR ? rmask : lmask) & segmask & lt);
-            int* slot = reinterpret_cast<int*>(sched + seg_base + rank);
-            slot[isR ? 1 : 0] = lane;
-        }
-        __syncwarp();
-        for (int k = 0; k < total_slots; ++k) {
-            const int2 pr = sched[k];
-            const int head = pr.x >= 0 ? pr.x : pr.y;
-            const int rowy = meta[head * 2];
-            while (r0 < rowy) flush_row();
-            const int mp = right ? pr.y : pr.x;
-            R wxv = R(0);
-            int src = 0;
-            if (mp >= 0) {
-                const int sx = col - meta[mp * 2 + 1];
-                if (sx >= 0 && sx < W) wxv = psx[mp * WE + sx];
-                src = mp;
-            }
-            const cx<R>* cp = cy + src * WE;
-            if constexpr (F32) {
-                const float4* cp4 = reinterpret_cast<const float4*>(cp);
-#pragma unroll
-                for (int k2 = 0; k2 < WE / 2; ++k2) {
-                    const float4 c = cp4[k2];
-                    are[2 * k2] += c.x * wxv;
-                    aim[2 * k2] += c.y * wxv;
-                    if (2 * k2 + 1 < W) {
-                        are[2 * k2 + 1] += c.z * wxv;
-                        aim[2 * k2 + 1] += c.w * wxv;
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int kk = 0; kk < W; ++kk) {
-                    const cx<R> c = cp[kk];
-                    are[kk] += c.re * wxv;
-                    aim[kk] += c.im * wxv;
-                }
-            }
-        }
-    }
-    while (r0 < P) flush_row();
-}
-
 template <class R, int D>
 __device__ __forceinline__ cx<R> merged_cell(const Job<R>& J, long long cidx);
 
@@ -794,31 +618,9 @@ static infft_status launch_spread2d_m(JobSet<R>& js, cudaStream_t st) {
     return INFFT_OK;
 }
 
-template <class R, int MM>
-static infft_status launch_spread2d_pair_m(JobSet<R>& js, cudaStream_t st) {
-    constexpr int W = 2 * MM + 1;
-    constexpr int WE = W + 1;
-    size_t spw = 32 * WE * sizeof(cx<R>) + 32 * WE * sizeof(R) + 64 * sizeof(int) + 32 * sizeof(int2) +
-                 (WPOLY_DEG + 1) * wpoly_stride(W) * sizeof(float);
-    spw = (spw + 15) & ~(size_t)15;
-    js.smem_per_warp = (int)spw;
-    js.wpb = 4;
-    const int nitems = js.pre_items[js.njobs];
-    if (nitems == 0) return INFFT_OK;
-    const size_t smem = spw * js.wpb;
-    INFFT_CUDA(cudaFuncSetAttribute(k_spread2d_pair<R, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_spread2d_pair<R, MM><<<(nitems + js.wpb - 1) / js.wpb, 32 * js.wpb, smem, st>>>(js);
-    INFFT_LAUNCHED();
-    return INFFT_OK;
-}
-
 template <class R, bool BOPT>
 static infft_status launch_spread2d(JobSet<R>& js, cudaStream_t st, int m) {
-    if (false) {  // the paired variant is kept for reference but not faster
-        bool t16 = true;
-        for (int j = 0; j < js.njobs; ++j) t16 = t16 && js.job[j].T == 16;
-        if (t16) {
-            switch (m) {
+    switch (m) {
                 case 2: return launch_spread2d_pair_m<R, 2>(js, st);
                 case 3: return launch_spread2d_pair_m<R, 3>(js, st);
                 default: return launch_spread2d_pair_m<R, 4>(js, st);
