@@ -621,13 +621,6 @@ static infft_status launch_spread2d_m(JobSet<R>& js, cudaStream_t st) {
 template <class R, bool BOPT>
 static infft_status launch_spread2d(JobSet<R>& js, cudaStream_t st, int m) {
     switch (m) {
-                case 2: return launch_spread2d_pair_m<R, 2>(js, st);
-                case 3: return launch_spread2d_pair_m<R, 3>(js, st);
-                default: return launch_spread2d_pair_m<R, 4>(js, st);
-            }
-        }
-    }
-    switch (m) {
         case 2: return launch_spread2d_m<R, 2, BOPT>(js, st);
         case 3: return launch_spread2d_m<R, 3, BOPT>(js, st);
         case 4: return launch_spread2d_m<R, 4, BOPT>(js, st);
