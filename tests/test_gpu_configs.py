@@ -1,0 +1,77 @@
+"""Full-size workloads on the GPU, checked on sampled coefficients against the FP64
+oracle's exact sums with the same weights (the hot-path parity of Algorithm 3.7).
+
+* polar grid, d=2, M=128, 512 angles x 256 radii (N = 131072), FP32 spreading with m=4
+  and m=6, weights from the float64 CG at degree 2M (iterations capped: the polar
+  system is ill-conditioned, so only the residual is recorded);
+* stack of spirals, d=3, M=64, 64 planes x 32768 points (N = 2^21), FP32, m=4;
+* a batch of random sets up to M=256 executed through one CUDA graph.
+Exactness cannot hold on these grids, so the checks are parity with the oracle at the
+FP32 bound (1e-5) and finiteness / monotonicity of the CG residual.
+"""
+import numpy as np
+import pytest
+
+import inputs
+from oracle import fourier as FO
+from tests.gpu_util import lib_or_skip, rel, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def sampled_parity(x, w, f, M, d, h, nk, seed):
+    K = M ** d
+    ks = np.random.default_rng(seed).choice(K, size=min(nk, K), replace=False)
+    ref = FO.adjoint_ndft(x, w * f, M, k_subset=ks)
+    return rel(h.ravel()[ks], ref)
+
+
+@pytest.mark.parametrize("m", [4, 6])
+def test_polar_d2_M128(m):
+    L, torch = lib_or_skip()
+    x = inputs.polar(512, 256)
+    M = 128
+    p = L.Plan(x, M, 2.0, m, "fp32")
+    info = p.weights(max_iter=30, rel_tol=1e-13)
+    assert np.isfinite(info["residual_inf"])
+    w = p.get_weights()
+    assert np.all(np.isfinite(w))
+    f = inputs.samples_complex(x.shape[0], 3)
+    h = p.adjoint(to_dev(torch, f, torch.complex64), mode=L.MODE_DCF).cpu().numpy()
+    assert sampled_parity(x, w, f, M, 2, h, 256, 4) < 1e-5
+
+
+def test_spiral_stack_d3_M64():
+    L, torch = lib_or_skip()
+    x = inputs.spiral_stack(64, 32768, 64)
+    M = 64
+    p = L.Plan(x, M, 2.0, 4, "fp32")
+    info = p.weights(max_iter=8, rel_tol=1e-13)
+    assert np.isfinite(info["residual_inf"])
+    w = p.get_weights()
+    f = inputs.samples_complex(x.shape[0], 5)
+    h = p.adjoint(to_dev(torch, f, torch.complex64), mode=L.MODE_DCF).cpu().numpy()
+    assert sampled_parity(x, w, f, M, 3, h, 48, 6) < 1e-5
+
+
+def test_batched_graph_large_sets():
+    L, torch = lib_or_skip()
+    sets = inputs.batch_sets(6, 21)
+    sets[0] = (256, inputs.random_points(5 * 256 * 256, 2, 77))
+    plans, fs, hs, ws, fh = [], [], [], [], []
+    for i, (M, x) in enumerate(sets):
+        p = L.Plan(x, M, 2.0, 4, "fp32")
+        w = inputs.coeffs_complex((x.shape[0],), 300 + i) / x.shape[0]
+        p.set_weights(w)
+        f = inputs.samples_complex(x.shape[0], 400 + i)
+        plans.append(p)
+        ws.append(w)
+        fh.append(f)
+        fs.append(to_dev(torch, f, torch.complex64))
+        hs.append(torch.zeros((M, M), dtype=torch.complex64, device="cuda"))
+    b = L.Batch(plans, fs, hs, L.MODE_DCF)
+    for _ in range(3):
+        b.run()
+    torch.cuda.synchronize()
+    for i, (M, x) in enumerate(sets):
+        assert sampled_parity(x, ws[i], fh[i], M, 2, hs[i].cpu().numpy(), 128, 500 + i) < 1e-5
