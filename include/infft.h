@@ -31,7 +31,10 @@
  * Streams.  `stream` is a cudaStream_t passed as void*; NULL means the legacy
  * default stream.  Calls on device buffers are stream ordered and do not
  * synchronise the host, except where stated (plan creation, infft_weights,
- * infft_optimize_B and the getters synchronise).
+ * infft_optimize_B and the getters synchronise).  A plan's transforms write the
+ * plan's own scratch grids: transforms of one plan must not overlap in time, so
+ * enqueue them on one stream (or order the streams with events).  Different plans
+ * may run concurrently on different streams and host threads.
  *
  * Errors.  Every call returns an infft_status and never throws or aborts.
  * infft_last_error() returns a thread-local message for the last failing call.
@@ -163,11 +166,31 @@ infft_status infft_forward(infft_plan_t plan, const void* fhat, void* f, void* s
  * infft_adjoint_batched -- `count` reconstructions on (possibly different) plans
  * of the same d and precision, executed as one launch per kernel stage over
  * all of them.  f[i], fhat[i] are device pointers, or host pointers staged through
- * the plan's own I/O buffers (then a plan may appear only once in the batch and the
- * call synchronises).
+ * the plan's own I/O buffers (then that plan may appear only once in the batch,
+ * else INFFT_EINVAL, and the call synchronises).  A plan may appear several times
+ * with device buffers (several sample vectors on one point set, e.g. one per
+ * receive coil): its k-th occurrence uses the k-th set of scratch grids, allocated
+ * on first need and owned by the plan until infft_destroy (counted in
+ * infft_plan_device_bytes).  The fhat[i] must not overlap.
  */
 infft_status infft_adjoint_batched(const infft_plan_t* plans, int count, int mode,
                                    const void* const* f, void* const* fhat, void* stream);
+
+/*
+ * infft_adjoint_batched_slots -- as infft_adjoint_batched, with the scratch set of
+ * every job chosen by the caller: job i runs on scratch set slots[i] of its plan
+ * (0 = the plan's own, k >= 1 allocated on first need, at most
+ * INFFT_MAX_SCRATCH_SLOT).  Jobs of one plan in one call need distinct slots
+ * (else INFFT_EINVAL).  Transforms of one plan that may overlap in time (batches on
+ * different streams) are safe when they use different slots; that is the caller's
+ * promise, the library does not track streams.  The library's extension for
+ * schedulers that keep one point set in flight on several streams; the method
+ * itself (Algorithm 3.7) has no counterpart.
+ */
+#define INFFT_MAX_SCRATCH_SLOT 1024
+infft_status infft_adjoint_batched_slots(const infft_plan_t* plans, int count, int mode,
+                                         const void* const* f, void* const* fhat, const int* slots,
+                                         void* stream);
 
 /*
  * infft_adjoint_batched_timed -- as infft_adjoint_batched (count <= 96), and
@@ -183,7 +206,8 @@ infft_status infft_adjoint_batched_timed(const infft_plan_t* plans, int count, i
  * Graph-replayed batches.  infft_batch_create records the batched adjoint for
  * fixed plans and fixed device buffers f[i] / fhat[i] into a CUDA graph;
  * infft_batch_run replays it on `stream`.  The plans and buffers must outlive
- * the batch.
+ * the batch.  Plans may repeat as in infft_adjoint_batched; the extra scratch
+ * grids are allocated before the capture starts.
  */
 infft_status infft_batch_create(const infft_plan_t* plans, int count, int mode,
                                 const void* const* f, void* const* fhat, void* stream,

@@ -46,6 +46,8 @@ _SIGS = {
     "infft_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "infft_adjoint_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p),
                                         C.POINTER(C.c_void_p), C.c_void_p]),
+    "infft_adjoint_batched_slots": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p),
+                                              C.POINTER(C.c_void_p), C.POINTER(C.c_int), C.c_void_p]),
     "infft_adjoint_batched_timed": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p),
                                               C.POINTER(C.c_void_p), C.c_void_p, C.POINTER(C.c_float)]),
     "infft_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p),
@@ -138,6 +140,15 @@ def infft_adjoint_batched(plans, mode, f_ptrs, fhat_ptrs, stream=0):
     F = (C.c_void_p * n)(*f_ptrs)
     H = (C.c_void_p * n)(*fhat_ptrs)
     return load().infft_adjoint_batched(P, n, mode, F, H, stream)
+
+
+def infft_adjoint_batched_slots(plans, mode, f_ptrs, fhat_ptrs, slots, stream=0):
+    n = len(plans)
+    P = (C.c_void_p * n)(*plans)
+    F = (C.c_void_p * n)(*f_ptrs)
+    H = (C.c_void_p * n)(*fhat_ptrs)
+    S = (C.c_int * n)(*slots)
+    return load().infft_adjoint_batched_slots(P, n, mode, F, H, S, stream)
 
 
 def infft_destroy(plan):
@@ -261,9 +272,14 @@ class Plan:
         return f
 
 
-def adjoint_batched(plans, fs, fhats, mode: int = MODE_PLAIN, stream=None):
-    _check(infft_adjoint_batched([p.handle for p in plans], mode, [_ptr(f) for f in fs],
-                                 [_ptr(h) for h in fhats], _stream(stream)))
+def adjoint_batched(plans, fs, fhats, mode: int = MODE_PLAIN, stream=None, slots=None):
+    """Batched adjoint; `slots` (optional) picks the scratch set of each job."""
+    if slots is None:
+        _check(infft_adjoint_batched([p.handle for p in plans], mode, [_ptr(f) for f in fs],
+                                     [_ptr(h) for h in fhats], _stream(stream)))
+    else:
+        _check(infft_adjoint_batched_slots([p.handle for p in plans], mode, [_ptr(f) for f in fs],
+                                           [_ptr(h) for h in fhats], list(slots), _stream(stream)))
 
 
 def adjoint_batched_timed(plans, fs, fhats, mode: int = MODE_PLAIN, stream=None):

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdint>
 #include <string>
+#include <array>
 #include <vector>
 
 #include "common.cuh"
@@ -53,6 +54,10 @@ struct infft_plan_s {
     void* grid = nullptr;
     void* tmp1 = nullptr;
     void* tmp2 = nullptr;
+    size_t scratch_bytes[4] = {0, 0, 0, 0};   // sizes of padded, grid, tmp1, tmp2
+    // further scratch sets, used when one batched call names the plan more than once
+    // (slot k >= 1 is extra[k - 1]); allocated on first need and kept
+    std::vector<std::array<void*, 4>> extra;
     void* io_in = nullptr;    // staging for host inputs / outputs
     void* io_out = nullptr;
 
@@ -106,7 +111,7 @@ bool is_device_pointer(const void* ptr);
 
 // Build the Job descriptors of a list of plans for one transform each.
 template <class R>
-Job<R> make_job(const infft_plan_s* p, int mode, const void* in, void* out);
+Job<R> make_job(const infft_plan_s* p, int mode, const void* in, void* out, int slot = 0);
 
 // Execute transforms for jobs of one d and precision: the adjoint (spread -> merge ->
 // FFT passes with crop and deconvolution) or the forward NFFT (FFT passes with

@@ -243,7 +243,7 @@ __global__ void k_wpoly(int m, double beta, float* __restrict__ coef) {
 
 // ----------------------------------------------------------------------------------------
 template <class R>
-Job<R> make_job(const infft_plan_s* p, int mode, const void* in, void* out) {
+Job<R> make_job(const infft_plan_s* p, int mode, const void* in, void* out, int slot) {
     Job<R> J;
     memset(&J, 0, sizeof(J));
     J.d = p->d; J.M = p->M; J.Ms = p->Ms; J.m = p->m;
@@ -256,13 +256,19 @@ Job<R> make_job(const infft_plan_s* p, int mode, const void* in, void* out) {
     J.dinv = (mode == INFFT_MODE_BOPT && p->dinv_win) ? (const R*)p->dinv_win : (const R*)p->dinv;
     J.tw = (const cx<R>*)p->tw;
     J.wpoly = p->wpoly;
-    J.padded = (cx<R>*)p->padded; J.grid = (cx<R>*)p->grid;
-    J.tmp1 = (cx<R>*)p->tmp1; J.tmp2 = (cx<R>*)p->tmp2;
+    if (slot == 0) {
+        J.padded = (cx<R>*)p->padded; J.grid = (cx<R>*)p->grid;
+        J.tmp1 = (cx<R>*)p->tmp1; J.tmp2 = (cx<R>*)p->tmp2;
+    } else {
+        const std::array<void*, 4>& e = p->extra[slot - 1];
+        J.padded = (cx<R>*)e[0]; J.grid = (cx<R>*)e[1];
+        J.tmp1 = (cx<R>*)e[2]; J.tmp2 = (cx<R>*)e[3];
+    }
     J.in = (const cx<R>*)in; J.out = (cx<R>*)out;
     return J;
 }
-template Job<float> make_job<float>(const infft_plan_s*, int, const void*, void*);
-template Job<double> make_job<double>(const infft_plan_s*, int, const void*, void*);
+template Job<float> make_job<float>(const infft_plan_s*, int, const void*, void*, int);
+template Job<double> make_job<double>(const infft_plan_s*, int, const void*, void*, int);
 
 static void free_plan(infft_plan_s* p) {
     if (!p) return;
@@ -271,6 +277,9 @@ static void free_plan(infft_plan_s* p) {
                     p->tmp2, p->io_in, p->io_out, p->wpoly};
     for (void* q : ptrs)
         if (q) cudaFree(q);
+    for (const auto& e : p->extra)
+        for (void* q : e)
+            if (q) cudaFree(q);
     delete p;
 }
 
@@ -392,14 +401,18 @@ static infft_status build_plan(infft_plan_s* p, const double* x_in, cudaStream_t
     // scratch
     long long pd = 1, msd_ = 1;
     for (int t = 0; t < d; ++t) { pd *= p->P; msd_ *= Ms; }
-    INFFT_TRY(dev_alloc(p, &p->padded, std::max<size_t>(1, (size_t)p->nitems) * pd * C_sz));
-    INFFT_TRY(dev_alloc(p, &p->grid, (size_t)msd_ * C_sz));
+    p->scratch_bytes[0] = std::max<size_t>(1, (size_t)p->nitems) * pd * C_sz;
+    p->scratch_bytes[1] = (size_t)msd_ * C_sz;
+    INFFT_TRY(dev_alloc(p, &p->padded, p->scratch_bytes[0]));
+    INFFT_TRY(dev_alloc(p, &p->grid, p->scratch_bytes[1]));
     size_t t1 = 0, t2 = 0;
     if (d >= 2) t1 = (size_t)ipow(Ms, d - 1) * p->M;
     if (d == 3) t2 = (size_t)Ms * p->M * p->M;
     // forward direction uses (M, M, Ms)... sizes: pass0 out Ms*M^(d-1), pass1 out Ms^2*M^(d-2)
     if (d >= 2) t1 = std::max(t1, (size_t)Ms * (size_t)ipow(p->M, d - 1));
     if (d == 3) t2 = std::max(t2, (size_t)Ms * Ms * p->M);
+    p->scratch_bytes[2] = t1 * C_sz;
+    p->scratch_bytes[3] = t2 * C_sz;
     if (t1) INFFT_TRY(dev_alloc(p, &p->tmp1, t1 * C_sz));
     if (t2) INFFT_TRY(dev_alloc(p, &p->tmp2, t2 * C_sz));
     INFFT_CUDA(cudaStreamSynchronize(st));
@@ -547,9 +560,54 @@ static infft_status batched_jobs_check(const infft_plan_t* plans, int count, int
     return INFFT_OK;
 }
 
+// Scratch slot of every job: the k-th occurrence of a plan in the batch uses slot k
+// (slot 0 is the plan's own scratch, slots k >= 1 are allocated here on first need).
+// Host buffers are staged through the plan's I/O buffers, so a plan given a host
+// pointer may appear only once.  Allocates, so it runs before a graph capture begins.
+static infft_status prepare_batched(const infft_plan_t* plans, int count, const void* const* f,
+                                    void* const* fhat, const int* slots_in, std::vector<int>& slot) {
+    slot.assign(count, 0);
+    for (int i = 0; i < count; ++i) {
+        if (slots_in) {
+            slot[i] = slots_in[i];
+            if (slot[i] < 0 || slot[i] > INFFT_MAX_SCRATCH_SLOT) {
+                set_error("scratch slot %d of job %d outside [0, %d]", slot[i], i, INFFT_MAX_SCRATCH_SLOT);
+                return INFFT_EINVAL;
+            }
+            for (int j = 0; j < i; ++j)
+                if (plans[j] == plans[i] && slot[j] == slot[i]) {
+                    set_error("jobs %d and %d share a plan and scratch slot %d", j, i, slot[i]);
+                    return INFFT_EINVAL;
+                }
+        } else {
+            for (int j = 0; j < i; ++j)
+                if (plans[j] == plans[i]) slot[i] = std::max(slot[i], slot[j] + 1);
+        }
+        const bool host = !is_device_pointer(f[i]) || !is_device_pointer(fhat[i]);
+        if (host) {
+            for (int j = 0; j < count; ++j)
+                if (j != i && plans[j] == plans[i]) {
+                    set_error("plan of job %d appears more than once and has host buffers", i);
+                    return INFFT_EINVAL;
+                }
+            INFFT_TRY(ensure_io(plans[i]));
+        }
+        infft_plan_s* p = plans[i];
+        while ((int)p->extra.size() < slot[i]) {
+            std::array<void*, 4> e{nullptr, nullptr, nullptr, nullptr};
+            p->extra.push_back(e);
+            for (int q = 0; q < 4; ++q)
+                if (p->scratch_bytes[q]) INFFT_TRY(dev_alloc(p, &p->extra.back()[q], p->scratch_bytes[q]));
+        }
+    }
+    return INFFT_OK;
+}
+
 static infft_status run_batched(const infft_plan_t* plans, int count, int mode, const void* const* f,
-                                void* const* fhat, cudaStream_t st, cudaEvent_t* ev = nullptr) {
-    // host buffers are staged through each plan's I/O buffers (a plan may then appear once)
+                                void* const* fhat, cudaStream_t st, cudaEvent_t* ev = nullptr,
+                                const int* slots_in = nullptr) {
+    std::vector<int> slot;
+    INFFT_TRY(prepare_batched(plans, count, f, fhat, slots_in, slot));
     std::vector<const void*> fin(count);
     std::vector<void*> fout(count);
     bool any_host_out = false;
@@ -559,7 +617,6 @@ static infft_status run_batched(const infft_plan_t* plans, int count, int mode, 
         fin[i] = f[i];
         fout[i] = fhat[i];
         const bool in_dev = is_device_pointer(f[i]), out_dev = is_device_pointer(fhat[i]);
-        if (!in_dev || !out_dev) INFFT_TRY(ensure_io(p));
         if (!in_dev) {
             INFFT_CUDA(cudaMemcpyAsync(p->io_in, f[i], (size_t)p->N * C, cudaMemcpyHostToDevice, st));
             fin[i] = p->io_in;
@@ -569,11 +626,11 @@ static infft_status run_batched(const infft_plan_t* plans, int count, int mode, 
     infft_status s;
     if (plans[0]->fp64) {
         std::vector<Job<double>> jobs;
-        for (int i = 0; i < count; ++i) jobs.push_back(make_job<double>(plans[i], mode, fin[i], fout[i]));
+        for (int i = 0; i < count; ++i) jobs.push_back(make_job<double>(plans[i], mode, fin[i], fout[i], slot[i]));
         s = run_jobs<double>(jobs, st, false, ev);
     } else {
         std::vector<Job<float>> jobs;
-        for (int i = 0; i < count; ++i) jobs.push_back(make_job<float>(plans[i], mode, fin[i], fout[i]));
+        for (int i = 0; i < count; ++i) jobs.push_back(make_job<float>(plans[i], mode, fin[i], fout[i], slot[i]));
         s = run_jobs<float>(jobs, st, false, ev);
     }
     if (s != INFFT_OK) return s;
@@ -617,12 +674,23 @@ infft_status infft_adjoint_batched(const infft_plan_t* plans, int count, int mod
     return run_batched(plans, count, mode, f, fhat, (cudaStream_t)stream);
 }
 
+infft_status infft_adjoint_batched_slots(const infft_plan_t* plans, int count, int mode, const void* const* f,
+                                         void* const* fhat, const int* slots, void* stream) {
+    INFFT_TRY(batched_jobs_check(plans, count, mode));
+    if (!f || !fhat) { set_error("null buffers"); return INFFT_EINVAL; }
+    return run_batched(plans, count, mode, f, fhat, (cudaStream_t)stream, nullptr, slots);
+}
+
 infft_status infft_batch_create(const infft_plan_t* plans, int count, int mode, const void* const* f,
                                 void* const* fhat, void* stream, infft_batch_t* out) {
     if (!out) { set_error("out is NULL"); return INFFT_EINVAL; }
     *out = nullptr;
     INFFT_TRY(batched_jobs_check(plans, count, mode));
     if (!f || !fhat) { set_error("null buffers"); return INFFT_EINVAL; }
+    {
+        std::vector<int> slot;   // allocations happen outside the capture
+        INFFT_TRY(prepare_batched(plans, count, f, fhat, nullptr, slot));
+    }
     cudaStream_t cap;
     INFFT_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     infft_batch_s* b = new infft_batch_s();

@@ -1,0 +1,322 @@
+"""Continuous-batching request loop for reconstructions h = D^* F^* B^* W f (Algorithm 3.7).
+
+Requests name a point set and carry a sample vector f.  The loop keeps plans (sorted
+points, weights, tables) on the device across requests; a request for an unknown point
+set is parked while a worker thread builds its plan and weights (Algorithm 3.6) on a
+stream of its own.  Every iteration of ``step()``:
+
+* retires batches whose completion event has fired and stamps their latencies;
+* admits ready requests into a new batch as soon as one of the ``streams`` slots is free
+  (so requests that arrive while earlier batches run are batched and overlap with them
+  on the device), grouping requests by (d, precision) and launching each group as one
+  batched adjoint (``infft_adjoint_batched``);
+* before a new plan is built, frees least-recently-used cached plans with no queued or
+  running request until the estimated device memory fits the budget (memory-based
+  admission); plans being built hold their estimate meanwhile.
+
+Transforms of one plan that overlap in time need separate scratch grids: every request
+in flight is given its own scratch set of the plan (``infft_adjoint_batched_slots``), so
+one point set can be in several running batches and repeat within a batch.
+
+The compute happens in the CUDA library; this module only schedules calls.  The backend
+is injectable so that the scheduling logic can be tested without a GPU.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import queue
+import threading
+import time
+from typing import Any, Callable, Dict, List, Optional
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    key: Any                 # point-set identifier
+    f: Any                   # sample vector (device tensor)
+    t_arrive: float = 0.0
+    t_admit: float = 0.0
+    t_done: float = 0.0
+    out: Any = None
+    batch_size: int = 0
+
+
+@dataclasses.dataclass
+class PointSet:
+    """What the loop needs to know about a point set before its plan exists."""
+    key: Any
+    d: int
+    M: int
+    x: Any                   # N x d float64 (host)
+    precision: str = "fp32"
+
+
+class Backend:
+    """GPU backend over the library: plans, batched launches, completion events."""
+
+    def __init__(self, weights_iters: int = 30, m: int = 4, sigma: float = 2.0):
+        import torch
+
+        import paper_2302_00414_gb300 as L
+        self.torch, self.L = torch, L
+        self.weights_iters, self.m, self.sigma = weights_iters, m, sigma
+        L.load()
+
+    def build_plan(self, ps: PointSet, stream):
+        p = self.L.Plan(ps.x, ps.M, self.sigma, self.m, ps.precision, stream=stream.cuda_stream)
+        p.weights(max_iter=self.weights_iters, rel_tol=1e-12, stream=stream.cuda_stream)
+        return p
+
+    def plan_bytes(self, plan) -> int:
+        return plan.device_bytes
+
+    def estimate_bytes(self, ps: PointSet) -> int:
+        n = ps.x.shape[0]
+        grid = (2 * ps.M) ** ps.d
+        cg = 16 * ((4 * ps.M) ** ps.d) * 8   # float64 grids and scratch of the degree-2M solve
+        return 120 * n + 40 * grid + cg
+
+    def free_bytes(self) -> int:
+        return int(self.torch.cuda.mem_get_info()[0])
+
+    def new_stream(self):
+        return self.torch.cuda.Stream()
+
+    def launch(self, plans, fs, stream, slots):
+        torch = self.torch
+        with torch.cuda.stream(stream):
+            # outputs allocated on the launch stream; inputs marked as used by it
+            outs = [torch.empty((p.M,) * p.d, dtype=f.dtype, device=f.device) for p, f in zip(plans, fs)]
+            for f in fs:
+                f.record_stream(stream)
+            self.L.adjoint_batched(plans, fs, outs, self.L.MODE_DCF, stream=stream.cuda_stream, slots=slots)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        return outs, ev
+
+    def done(self, ev) -> bool:
+        return ev.query()
+
+    def release(self, plan):
+        plan.close()
+
+
+class Server:
+    def __init__(self, backend, mem_budget: Optional[int] = None, max_batch: int = 64, streams: int = 3,
+                 max_repeat: int = 8, clock: Callable[[], float] = time.perf_counter):
+        self.be = backend
+        self.max_batch = max_batch
+        self.max_repeat = max_repeat
+        self.mem_budget = mem_budget
+        self.clock = clock
+        self.streams = [backend.new_stream() for _ in range(streams)]
+        self.free_streams = list(range(streams))
+        self.plans: Dict[Any, Any] = {}
+        self.plan_meta: Dict[Any, PointSet] = {}
+        self.plan_used: Dict[Any, float] = {}
+        self.plan_size: Dict[Any, int] = {}
+        self.plan_refs: Dict[Any, int] = collections.Counter()   # requests queued or in flight
+        self.resident_bytes = 0        # plans on the device
+        self.reserved: Dict[Any, int] = {}   # estimates of plans being built
+        self.pending: collections.deque = collections.deque()
+        self.parked: Dict[Any, List[Request]] = collections.defaultdict(list)
+        self.inflight: List[tuple] = []
+        self.completed: List[Request] = []
+        self.stats = collections.Counter()
+        self._retry: List[PointSet] = []
+        self._lock = threading.Lock()
+        self._work: queue.Queue = queue.Queue()
+        self._ready: queue.Queue = queue.Queue()
+        self._pstream = backend.new_stream()
+        self._worker = threading.Thread(target=self._precompute_loop, daemon=True)
+        self._worker.start()
+
+    # ---- admission of point sets ------------------------------------------------------
+    def register(self, ps: PointSet):
+        self.plan_meta[ps.key] = ps
+
+    def _precompute_loop(self):
+        while True:
+            ps = self._work.get()
+            if ps is None:
+                return
+            try:
+                plan = self.be.build_plan(ps, self._pstream)
+                self._ready.put((ps.key, plan, None))
+            except Exception as e:  # surfaced to the requests of this key
+                self._ready.put((ps.key, None, e))
+
+    def _make_room(self, need: int) -> bool:
+        """Evict LRU plans that are not in flight until `need` more bytes fit."""
+        def fits():
+            held = self.resident_bytes + sum(self.reserved.values())
+            if self.mem_budget is not None and held + need > self.mem_budget:
+                return False
+            return self.be.free_bytes() - sum(self.reserved.values()) > need
+        while not fits():
+            idle = [k for k in self.plans if self.plan_refs[k] == 0]
+            if not idle:
+                return False
+            victim = min(idle, key=lambda k: self.plan_used[k])
+            plan = self.plans.pop(victim)
+            self.resident_bytes -= self.plan_size.pop(victim)
+            self.be.release(plan)
+            self.stats["evicted"] += 1
+        return True
+
+    def submit(self, req: Request):
+        req.t_arrive = req.t_arrive or self.clock()
+        if req.key in self.plans:
+            self.plan_refs[req.key] += 1
+            self.pending.append(req)
+            return
+        first = req.key not in self.parked or not self.parked[req.key]
+        self.parked[req.key].append(req)
+        if first:
+            ps = self.plan_meta[req.key]
+            self.stats["new_sets"] += 1
+            self._deferred_admit(ps)
+
+    def _deferred_admit(self, ps: PointSet):
+        need = self.be.estimate_bytes(ps)
+        if self._make_room(need):
+            self.reserved[ps.key] = need
+            self._work.put(ps)
+        elif not self.plans and not self.reserved:
+            raise MemoryError(f"point set {ps.key!r} needs ~{need} bytes, more than the budget")
+        else:
+            self.stats["admit_deferred"] += 1
+            self._retry.append(ps)
+
+    # ---- the loop ------------------------------------------------------------------------
+    def step(self) -> int:
+        """Retire finished batches, absorb new plans, launch ready requests; returns the
+        number of requests still queued or in flight."""
+        now = self.clock
+        # finished batches
+        still = []
+        for ev, reqs, sidx, outs in self.inflight:
+            if self.be.done(ev):
+                t = now()
+                for r, o in zip(reqs, outs):
+                    r.t_done, r.out = t, o
+                    self.plan_refs[r.key] -= 1
+                    self.completed.append(r)
+                self.free_streams.append(sidx)
+            else:
+                still.append((ev, reqs, sidx, outs))
+        self.inflight = still
+        # plans built by the worker
+        while True:
+            try:
+                key, plan, err = self._ready.get_nowait()
+            except queue.Empty:
+                break
+            if err is not None:
+                raise err
+            self.reserved.pop(key, None)
+            self.plans[key] = plan
+            self.plan_used[key] = now()
+            self.plan_size[key] = self.be.plan_bytes(plan)
+            self.resident_bytes += self.plan_size[key]
+            waiting = self.parked.pop(key, [])
+            self.plan_refs[key] += len(waiting)
+            self.pending.extend(waiting)
+        if self._retry:
+            retry, self._retry = self._retry, []
+            for ps in retry:
+                self._deferred_admit(ps)
+        # launch: one batch per (d, precision) group into free stream slots.  The j-th
+        # request for a point set in the batch on stream s uses the plan's scratch set
+        # s * max_repeat + j, so batches on different streams never share scratch.
+        while self.pending and self.free_streams:
+            groups: Dict[tuple, List[Request]] = collections.OrderedDict()
+            per_key: Dict[Any, int] = collections.Counter()
+            keep = []
+            n = 0
+            while self.pending and n < self.max_batch:
+                r = self.pending.popleft()
+                if per_key[r.key] >= self.max_repeat:
+                    keep.append(r)
+                    continue
+                ps = self.plan_meta[r.key]
+                groups.setdefault((ps.d, ps.precision), []).append(r)
+                per_key[r.key] += 1
+                n += 1
+            self.pending.extendleft(reversed(keep))
+            if not groups:
+                break
+            for reqs in groups.values():
+                if not self.free_streams:
+                    self.pending.extendleft(reversed(reqs))
+                    continue
+                sidx = self.free_streams.pop()
+                plans = [self.plans[r.key] for r in reqs]
+                t = now()
+                for r in reqs:
+                    r.t_admit = t
+                    r.batch_size = len(reqs)
+                    self.plan_used[r.key] = t
+                occ: Dict[Any, int] = collections.Counter()
+                slots = []
+                for r in reqs:
+                    slots.append(sidx * self.max_repeat + occ[r.key])
+                    occ[r.key] += 1
+                outs, ev = self.be.launch(plans, [r.f for r in reqs], self.streams[sidx], slots)
+                for k in {r.key for r in reqs}:   # repeats may have grown the plan's scratch
+                    b = self.be.plan_bytes(self.plans[k])
+                    self.resident_bytes += b - self.plan_size.get(k, b)
+                    self.plan_size[k] = b
+                self.inflight.append((ev, reqs, sidx, outs))
+                self.stats["batches"] += 1
+                self.stats["max_inflight"] = max(self.stats["max_inflight"], len(self.inflight))
+        return len(self.pending) + sum(len(v) for v in self.parked.values()) + \
+            sum(len(r) for _, r, _, _ in self.inflight)
+
+    def drain(self, timeout: float = 600.0):
+        t0 = time.perf_counter()
+        while self.step() > 0:
+            if time.perf_counter() - t0 > timeout:
+                raise TimeoutError("requests did not complete")
+            time.sleep(0)
+
+    def close(self):
+        self._work.put(None)
+        self._worker.join(timeout=5)
+
+
+def run_poisson(server: Server, requests: List[Request], rate: float, seed: int = 0,
+                clock: Callable[[], float] = time.perf_counter) -> List[Request]:
+    """Feed `requests` at Poisson arrival times of mean rate `rate` (per second) while
+    stepping the server; returns the completed requests."""
+    import random
+    rng = random.Random(seed)
+    t = clock()
+    arrivals = []
+    for r in requests:
+        t += rng.expovariate(rate)
+        arrivals.append((t, r))
+    i = 0
+    while i < len(arrivals) or server.step() > 0:
+        now = clock()
+        while i < len(arrivals) and arrivals[i][0] <= now:
+            arrivals[i][1].t_arrive = arrivals[i][0]
+            server.submit(arrivals[i][1])
+            i += 1
+        server.step()
+    return server.completed
+
+
+def latency_summary(reqs: List[Request]) -> dict:
+    lat = sorted((r.t_done - r.t_arrive) * 1e3 for r in reqs)
+    if not lat:
+        return {}
+
+    def pct(q):
+        return lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
+    span = max(r.t_done for r in reqs) - min(r.t_arrive for r in reqs)
+    return {"requests": len(lat), "p50_ms": pct(0.50), "p99_ms": pct(0.99), "max_ms": lat[-1],
+            "throughput_per_s": len(lat) / span if span > 0 else None,
+            "mean_batch": sum(r.batch_size for r in reqs) / len(reqs)}

@@ -1,0 +1,166 @@
+"""Scheduling logic of the continuous-batching loop, with a fake backend (no GPU)."""
+import time
+
+import numpy as np
+
+from paper_2302_00414_gb300.serve import PointSet, Request, Server, latency_summary
+
+
+class FakeEvent:
+    def __init__(self, ticks):
+        self.ticks = ticks
+
+
+class FakePlan:
+    def __init__(self, ps):
+        self.M, self.d, self.key = ps.M, ps.d, ps.key
+
+
+class FakeBackend:
+    """Plans cost 100 bytes; a launched batch finishes after `latency` polls."""
+
+    def __init__(self, latency=3, free=10 ** 9):
+        self.latency, self.free = latency, free
+        self.built, self.launches, self.released, self.slots = [], [], [], []
+
+    def build_plan(self, ps, stream):
+        self.built.append(ps.key)
+        return FakePlan(ps)
+
+    def plan_bytes(self, plan):
+        return 100
+
+    def estimate_bytes(self, ps):
+        return 100
+
+    def free_bytes(self):
+        return self.free
+
+    def new_stream(self):
+        return object()
+
+    def launch(self, plans, fs, stream, slots):
+        self.launches.append([p.key for p in plans])
+        self.slots.append(list(slots))
+        return [("h", p.key, f) for p, f in zip(plans, fs)], FakeEvent(self.latency)
+
+    def done(self, ev):
+        ev.ticks -= 1
+        return ev.ticks <= 0
+
+    def release(self, plan):
+        self.released.append(plan.key)
+
+
+def sets(n, d=2):
+    return [PointSet(key=k, d=d, M=8, x=np.zeros((10, d))) for k in range(n)]
+
+
+def run(server, reqs, timeout=30.0):
+    for r in reqs:
+        server.submit(r)
+    server.drain(timeout=timeout)
+    return server.completed
+
+
+def test_all_complete_batched_and_overlapping():
+    be = FakeBackend(latency=4)
+    s = Server(be, max_batch=8, streams=3)
+    for ps in sets(3):
+        s.register(ps)
+    reqs = [Request(rid=i, key=i % 3, f=i) for i in range(50)]
+    done = run(s, reqs)
+    assert sorted(r.rid for r in done) == list(range(50))
+    assert all(r.out[1] == r.key and r.out[2] == r.f for r in done)
+    assert s.stats["new_sets"] == 3 and sorted(be.built) == [0, 1, 2]
+    assert max(len(b) for b in be.launches) > 1      # requests were batched
+    assert s.stats["max_inflight"] >= 2              # batches overlapped
+    assert latency_summary(done)["requests"] == 50
+    s.close()
+
+
+def test_requests_arriving_while_busy_join_later_batches():
+    be = FakeBackend(latency=5)
+    s = Server(be, max_batch=4, streams=1)
+    for ps in sets(1):
+        s.register(ps)
+    for i in range(3):
+        s.submit(Request(rid=i, key=0, f=i))
+    t0 = time.perf_counter()
+    while not s.inflight and time.perf_counter() - t0 < 30:   # plan built on the worker
+        s.step()
+    assert len(s.inflight) == 1
+    for i in range(3, 9):          # arrive while the first batch runs
+        s.submit(Request(rid=i, key=0, f=i))
+    s.drain(timeout=30)
+    assert sorted(r.rid for r in s.completed) == list(range(9))
+    assert len(be.launches) >= 2
+    s.close()
+
+
+def test_memory_admission_evicts_idle_plans():
+    be = FakeBackend(latency=1)
+    s = Server(be, mem_budget=250, max_batch=4, streams=2)   # two plans fit
+    for ps in sets(4):
+        s.register(ps)
+    done = run(s, [Request(rid=i, key=i, f=i) for i in range(4)])
+    assert sorted(r.rid for r in done) == [0, 1, 2, 3]
+    assert s.stats["evicted"] >= 2
+    assert s.resident_bytes <= 250
+    s.close()
+
+
+def test_groups_by_dimension():
+    be = FakeBackend(latency=2)
+    s = Server(be, max_batch=16, streams=4)
+    for ps in sets(2, d=2) + [PointSet(key=10, d=3, M=8, x=np.zeros((10, 3)))]:
+        s.register(ps)
+    run(s, [Request(rid=i, key=[0, 1, 10][i % 3], f=i) for i in range(12)])
+    for batch in be.launches:
+        dims = {(3 if k == 10 else 2) for k in batch}
+        assert len(dims) == 1
+    s.close()
+
+
+def test_running_transforms_never_share_scratch():
+    class Checking(FakeBackend):
+        def __init__(self):
+            super().__init__(latency=3)
+            self.running = []          # (event, {(key, slot)})
+
+        def launch(self, plans, fs, stream, slots):
+            live = set()
+            for ev, used in self.running:
+                if ev.ticks > 0:
+                    live |= used
+            used = [(p.key, s) for p, s in zip(plans, slots)]
+            assert len(set(used)) == len(used), "two jobs of a batch share a scratch set"
+            assert not (set(used) & live), "a scratch set in use was given to a new batch"
+            outs, ev = super().launch(plans, fs, stream, slots)
+            self.running.append((ev, set(used)))
+            return outs, ev
+
+    be = Checking()
+    s = Server(be, max_batch=16, streams=3, max_repeat=4)
+    for ps in sets(2):
+        s.register(ps)
+    done = run(s, [Request(rid=i, key=0 if i % 5 else 1, f=i) for i in range(60)])
+    assert sorted(r.rid for r in done) == list(range(60))
+    for batch in be.launches:
+        assert max(batch.count(k) for k in set(batch)) <= 4
+    assert max(len(b) for b in be.launches) > 1
+    assert s.stats["max_inflight"] >= 2      # the hot point set ran on several streams
+    s.close()
+
+
+def test_over_budget_point_set_is_an_error():
+    be = FakeBackend()
+    s = Server(be, mem_budget=50)
+    s.register(sets(1)[0])
+    try:
+        s.submit(Request(rid=0, key=0, f=0))
+    except MemoryError:
+        pass
+    else:
+        raise AssertionError("expected MemoryError")
+    s.close()
