@@ -255,6 +255,165 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Three-dimensional spreading (window modes), tiles of 8^3 cells.  One warp per work item,
+// the item's padded tile of P^3 cells (P = 8 + 2m + 1) in shared memory.  Lane l takes
+// the (z, x) tap pairs q = l + 32 r of a point (W^2 pairs, ceil(W^2 / 32) rounds) and
+// holds the W cells of each pair along y in registers, adding (c_j psi_y) psi_z psi_x.
+// The items' points are sorted by base cell: while consecutive points share their base
+// cell the registers keep accumulating; when it changes, the lanes store their cells,
+// meet at a __syncwarp and load the cells of the new base.  Each cell is summed in the
+// item's point order (deterministic, no atomics) and shared memory is touched once per
+// base cell rather than once per point.
+// The z-planes of the shared tile are PZ >= P^2 cells apart with PZ = W (mod 16), so the
+// cells of 16 consecutive pairs, at q + const (mod 16) in 8-byte units, fall into
+// distinct bank pairs: no bank conflicts.  The tile is written out densely (P^3).
+__host__ __device__ constexpr int spread3d_plane(int P, int W) { return P * P + (((W - P * P) % 16) + 16) % 16; }
+constexpr int SPREAD3D_T = 8;
+
+template <class R, int MM>
+__global__ void __launch_bounds__(64) k_spread3d(const __grid_constant__ JobSet<R> js) {
+    constexpr int W = 2 * MM + 1;
+    constexpr int WE = W + 1;                  // even stride of the staged rows
+    constexpr int NR = (W * W + 31) / 32;      // rounds over the (z, x) pairs
+    constexpr int T = SPREAD3D_T;
+    constexpr int P = T + 2 * MM + 1, P2 = P * P;
+    constexpr int PZ = spread3d_plane(P, W), SC = P * PZ;
+    constexpr bool F32 = sizeof(R) == 4;
+    using V2 = typename std::conditional<F32, float2, double2>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gitem = blockIdx.x * js.wpb + warp;
+    if (gitem >= js.pre_items[js.njobs]) return;
+    const int jb = find_job(js.pre_items, js.njobs, gitem);
+    const Job<R>& J = js.job[jb];
+    const int it = gitem - js.pre_items[jb];
+    const int4 item = J.items[it];
+    const int Ms = J.Ms, nt = J.ntile;
+
+    unsigned char* base = smem_raw + (size_t)warp * js.smem_per_warp;
+    V2* pad = reinterpret_cast<V2*>(base);                             // [P][PZ]
+    V2* cyv = pad + ((SC + 1) & ~1);                                   // [32][WE] c_j psi_y
+    R* psz = reinterpret_cast<R*>(cyv + 32 * WE);                      // [32][WE]
+    R* psx = psz + 32 * WE;                                            // [32][WE]
+    int* meta = reinterpret_cast<int*>(psx + 32 * WE);                 // [32] base cell in the shared tile
+    float* poly = reinterpret_cast<float*>(meta + 32);                 // window polynomial (float32 plans)
+    const bool use_poly = F32 && J.wpoly != nullptr;
+    if (use_poly) {
+        for (int e = lane; e < (WPOLY_DEG + 1) * wpoly_stride(W); e += 32) poly[e] = J.wpoly[e];
+    }
+    for (int e = lane; e < SC; e += 32) { pad[e].x = R(0); pad[e].y = R(0); }
+
+    const int tz = item.x / (nt * nt), ty = (item.x / nt) % nt, tx = item.x % nt;
+    const int logMs = 31 - __clz(Ms);
+    int off[NR], sz[NR], sx[NR];
+    bool ok[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int q = lane + 32 * r;
+        ok[r] = q < W * W;
+        sz[r] = ok[r] ? q / W : 0;
+        sx[r] = ok[r] ? q % W : 0;
+        off[r] = sz[r] * PZ + sx[r];
+    }
+    V2 v[NR][W];
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int s = 0; s < W; ++s) { v[r][s].x = R(0); v[r][s].y = R(0); }
+    int cur = -1;
+
+    for (int c0 = 0; c0 < item.z; c0 += 32) {
+        const int np = min(32, item.z - c0);
+        __syncwarp();
+        if (lane < np) {
+            const int i = item.y + c0 + lane;
+            const int j = __ldg(J.perm + i);
+            cx<R> fv = J.in[j];
+            if (J.mode == INFFT_MODE_DCF) fv = mul(J.w[i], fv);
+            const uint32_t cl = __ldg(J.cell + i);
+            const int cxl = (int)(cl & (uint32_t)(Ms - 1));
+            const int cyl = (int)((cl >> logMs) & (uint32_t)(Ms - 1));
+            const int czl = (int)(cl >> (2 * logMs));
+            meta[lane] = (czl - tz * T) * PZ + (cyl - ty * T) * P + (cxl - tx * T);
+            const R uz = J.u[(size_t)i * 3 + 0], uy = J.u[(size_t)i * 3 + 1], ux = J.u[(size_t)i * 3 + 2];
+            R wz[W], wy[W], wx[W];
+            bool done = false;
+            if constexpr (F32) {
+                if (use_poly) {
+                    poly_taps2<W>(poly, uz, uy, wz, wy);
+                    poly_taps<W>(poly, ux, wx);
+                    done = true;
+                }
+            }
+            if (!done) {
+#pragma unroll
+                for (int s = 0; s < W; ++s) {
+                    wz[s] = tap_weight<R>(J.window, uz, s, MM, J.inv_m, J.beta);
+                    wy[s] = tap_weight<R>(J.window, uy, s, MM, J.inv_m, J.beta);
+                    wx[s] = tap_weight<R>(J.window, ux, s, MM, J.inv_m, J.beta);
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < W; ++s) {
+                cyv[lane * WE + s].x = fv.re * wy[s];
+                cyv[lane * WE + s].y = fv.im * wy[s];
+                psz[lane * WE + s] = wz[s];
+                psx[lane * WE + s] = wx[s];
+            }
+        }
+        __syncwarp();
+        for (int p = 0; p < np; ++p) {
+            const int b0 = meta[p];
+            if (b0 != cur) {   // uniform across the warp
+                if (cur >= 0) {
+#pragma unroll
+                    for (int r = 0; r < NR; ++r)
+                        if (ok[r]) {
+#pragma unroll
+                            for (int s = 0; s < W; ++s) pad[cur + off[r] + s * P] = v[r][s];
+                        }
+                }
+                __syncwarp();
+#pragma unroll
+                for (int r = 0; r < NR; ++r)
+                    if (ok[r]) {
+#pragma unroll
+                        for (int s = 0; s < W; ++s) v[r][s] = pad[b0 + off[r] + s * P];
+                    }
+                cur = b0;
+            }
+            V2 c[W];
+#pragma unroll
+            for (int s = 0; s < W; ++s) c[s] = cyv[p * WE + s];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const R w = psz[p * WE + sz[r]] * psx[p * WE + sx[r]];
+                if constexpr (F32) {
+                    const float2 ww = make_float2(w, w);
+#pragma unroll
+                    for (int s = 0; s < W; ++s) v[r][s] = __ffma2_rn(c[s], ww, v[r][s]);
+                } else {
+#pragma unroll
+                    for (int s = 0; s < W; ++s) { v[r][s].x += c[s].x * w; v[r][s].y += c[s].y * w; }
+                }
+            }
+        }
+    }
+    if (cur >= 0) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            if (ok[r]) {
+#pragma unroll
+                for (int s = 0; s < W; ++s) pad[cur + off[r] + s * P] = v[r][s];
+            }
+    }
+    __syncwarp();
+    V2* dst = reinterpret_cast<V2*>(J.padded) + (size_t)it * P2 * P;
+    for (int z = 0; z < P; ++z)
+        for (int e = lane; e < P2; e += 32) dst[(size_t)z * P2 + e] = pad[z * PZ + e];
+}
+
 template <class R, int D>
 __device__ __forceinline__ cx<R> merged_cell(const Job<R>& J, long long cidx);
 
@@ -292,6 +451,46 @@ __global__ void __launch_bounds__(256) k_merge2d(const __grid_constant__ JobSet<
         }
     }
     J.grid[(size_t)(ty * T + r) * Ms + tx * T + c] = acc;
+}
+
+// ---------------------------------------------------------------------------------------
+// Three-dimensional merge, one block per tile of T^3 cells (T a power of two, m < T),
+// threads striding over the tile's cells.  Along an axis the cell at offset r of tile t
+// lies in the padded tile of t at r + m, of t - 1 at r + T + m when r <= m, and of t + 1
+// at r - T + m when r >= T - m; with T <= 2m both neighbours can hold it.  Work items of
+// a source tile are summed in item order, sources in a fixed order: deterministic.
+template <class R>
+__global__ void __launch_bounds__(256) k_merge3d(const __grid_constant__ JobSet<R> js) {
+    const int gblk = blockIdx.x;
+    const int jb = find_job(js.pre_merge, js.njobs, gblk);
+    const Job<R>& J = js.job[jb];
+    const int T = J.T, m = J.m, P = J.P, nt = J.ntile, Ms = J.Ms;
+    const int tile = gblk - js.pre_merge[jb];
+    const int tz = tile / (nt * nt), ty = (tile / nt) % nt, tx = tile % nt;
+    const int logT = 31 - __clz(T);
+    const size_t cells = (size_t)P * P * P;
+    for (int e = threadIdx.x; e < T * T * T; e += blockDim.x) {
+        const int rz = e >> (2 * logT), ry = (e >> logT) & (T - 1), rx = e & (T - 1);
+        const int rr[3] = {rz, ry, rx}, tt[3] = {tz, ty, tx};
+        int st[3][3], so[3][3], ns[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int r = rr[a], t = tt[a];
+            st[a][0] = t; so[a][0] = r + m; ns[a] = 1;
+            if (r <= m) { st[a][ns[a]] = (t - 1 + nt) % nt; so[a][ns[a]] = r + T + m; ++ns[a]; }
+            if (r >= T - m) { st[a][ns[a]] = (t + 1) % nt; so[a][ns[a]] = r - T + m; ++ns[a]; }
+        }
+        cx<R> acc = mk<R>(0, 0);
+        for (int a = 0; a < ns[0]; ++a)
+            for (int b = 0; b < ns[1]; ++b)
+                for (int c = 0; c < ns[2]; ++c) {
+                    const int tl = (st[0][a] * nt + st[1][b]) * nt + st[2][c];
+                    const int i0 = __ldg(J.tile_items + tl), i1 = __ldg(J.tile_items + tl + 1);
+                    const size_t off = ((size_t)so[0][a] * P + so[1][b]) * P + so[2][c];
+                    for (int itm = i0; itm < i1; ++itm) acc = add(acc, J.padded[(size_t)itm * cells + off]);
+                }
+        J.grid[((size_t)(tz * T + rz) * Ms + ty * T + ry) * Ms + tx * T + rx] = acc;
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -551,6 +750,100 @@ __global__ void __launch_bounds__(128) k_interp(const __grid_constant__ JobSet<R
 }
 
 // ---------------------------------------------------------------------------------------
+// Interpolation for d = 2, 3 with a fixed m: one warp per work item; the warp gathers the
+// padded tile of the grid around its tile into shared memory, then every lane sums the
+// W^d taps of one point in separable order (x innermost, then y, then z) and writes f_j
+// in the caller's order.  Window values come from the float32 polynomial or the exact
+// window (float64 plans).
+template <class R, int D, int MM>
+__global__ void __launch_bounds__(128) k_interp_t(const __grid_constant__ JobSet<R> js) {
+    constexpr int W = 2 * MM + 1;
+    constexpr bool F32 = sizeof(R) == 4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gitem = blockIdx.x * js.wpb + warp;
+    if (gitem >= js.pre_items[js.njobs]) return;
+    const int jb = find_job(js.pre_items, js.njobs, gitem);
+    const Job<R>& J = js.job[jb];
+    const int4 item = J.items[gitem - js.pre_items[jb]];
+    const int P = J.P, m = J.m, Ms = J.Ms, T = J.T, nt = J.ntile;
+    const int cells = D == 3 ? P * P * P : P * P;
+    unsigned char* base = smem_raw + (size_t)warp * js.smem_per_warp;
+    cx<R>* pad = reinterpret_cast<cx<R>*>(base);
+    float* poly = reinterpret_cast<float*>(pad + ((cells + 1) & ~1));
+    const bool use_poly = F32 && J.wpoly != nullptr;
+    if (use_poly) {
+        for (int e = lane; e < (WPOLY_DEG + 1) * wpoly_stride(W); e += 32) poly[e] = J.wpoly[e];
+    }
+    int tz = 0, ty, tx;
+    if (D == 3) { tz = item.x / (nt * nt); ty = (item.x / nt) % nt; tx = item.x % nt; }
+    else { ty = item.x / nt; tx = item.x % nt; }
+    const int Mmask = Ms - 1;  // Ms is a power of two
+    for (int e = lane; e < cells; e += 32) {
+        const int ox = e % P, r1 = e / P;
+        const int oy = r1 % P, oz = r1 / P;
+        const int gx = (tx * T - m + ox) & Mmask, gy = (ty * T - m + oy) & Mmask;
+        size_t g = (size_t)gy * Ms + gx;
+        if (D == 3) g += (size_t)((tz * T - m + oz) & Mmask) * Ms * Ms;
+        pad[e] = J.grid[g];
+    }
+    __syncwarp();
+    const int logMs = 31 - __clz(Ms);
+    for (int c0 = 0; c0 < item.z; c0 += 32) {
+        const int np = min(32, item.z - c0);
+        if (lane >= np) continue;
+        const int i = item.y + c0 + lane;
+        const uint32_t cl = __ldg(J.cell + i);
+        const int ox = (int)(cl & (uint32_t)Mmask) - tx * T;
+        const int oy = (int)((cl >> logMs) & (uint32_t)Mmask) - ty * T;
+        const int oz = D == 3 ? (int)(cl >> (2 * logMs)) - tz * T : 0;
+        R wz[W], wy[W], wx[W];
+        const R uy = J.u[(size_t)i * D + D - 2], ux = J.u[(size_t)i * D + D - 1];
+        const R uz = D == 3 ? J.u[(size_t)i * D] : R(0);
+        bool done = false;
+        if constexpr (F32) {
+            if (use_poly) {
+                poly_taps2<W>(poly, uy, ux, wy, wx);
+                if (D == 3) poly_taps<W>(poly, uz, wz);
+                done = true;
+            }
+        }
+        if (!done) {
+#pragma unroll
+            for (int s = 0; s < W; ++s) {
+                wy[s] = tap_weight<R>(J.window, uy, s, MM, J.inv_m, J.beta);
+                wx[s] = tap_weight<R>(J.window, ux, s, MM, J.inv_m, J.beta);
+                if (D == 3) wz[s] = tap_weight<R>(J.window, uz, s, MM, J.inv_m, J.beta);
+            }
+        }
+        cx<R> acc = mk<R>(0, 0);
+        const int NZ = D == 3 ? W : 1;
+#pragma unroll 1
+        for (int sz = 0; sz < NZ; ++sz) {
+            cx<R> accy = mk<R>(0, 0);
+            const cx<R>* plane = pad + (size_t)(oz + sz) * P * P;
+#pragma unroll
+            for (int sy = 0; sy < W; ++sy) {
+                const cx<R>* row = plane + (oy + sy) * P + ox;
+                cx<R> t = mk<R>(0, 0);
+#pragma unroll
+                for (int sx = 0; sx < W; ++sx) {
+                    const cx<R> g = row[sx];
+                    t.re += wx[sx] * g.re;
+                    t.im += wx[sx] * g.im;
+                }
+                accy.re += wy[sy] * t.re;
+                accy.im += wy[sy] * t.im;
+            }
+            const R wzs = D == 3 ? wz[sz] : R(1);
+            acc.re += wzs * accy.re;
+            acc.im += wzs * accy.im;
+        }
+        J.out[__ldg(J.perm + i)] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // host drivers
 
 static int pick_lines(int n, size_t elem) {
@@ -645,6 +938,73 @@ static bool spread2d_eligible(const JobSet<R>& js, int* m_out, bool* bopt_out) {
     return true;
 }
 
+// three-dimensional spreading in window modes when every job has the same m (1..7)
+template <class R, int MM>
+static infft_status launch_spread3d_m(JobSet<R>& js, cudaStream_t st) {
+    constexpr int W = 2 * MM + 1;
+    constexpr int WE = W + 1;
+    constexpr int P = SPREAD3D_T + 2 * MM + 1;
+    const size_t cells = (size_t)P * spread3d_plane(P, W);
+    size_t spw = ((cells + 1) & ~(size_t)1) * sizeof(cx<R>) + 32 * WE * (sizeof(cx<R>) + 2 * sizeof(R)) +
+                 32 * sizeof(int) + (WPOLY_DEG + 1) * wpoly_stride(W) * sizeof(float);
+    spw = (spw + 15) & ~(size_t)15;
+    const size_t smem_cap = 200 * 1024;
+    if (spw > smem_cap) {
+        set_error("padded tile needs %zu bytes of shared memory", spw);
+        return INFFT_EUNSUPPORTED;
+    }
+    js.smem_per_warp = (int)spw;
+    js.wpb = spw > 48 * 1024 ? 1 : 2;
+    const int nitems = js.pre_items[js.njobs];
+    if (nitems == 0) return INFFT_OK;
+    const size_t smem = spw * js.wpb;
+    INFFT_CUDA(cudaFuncSetAttribute(k_spread3d<R, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_spread3d<R, MM><<<(nitems + js.wpb - 1) / js.wpb, 32 * js.wpb, smem, st>>>(js);
+    INFFT_LAUNCHED();
+    return INFFT_OK;
+}
+
+template <class R>
+static bool spread3d_eligible(const JobSet<R>& js, int* m_out) {
+    if (js.njobs < 1) return false;
+    const int m = js.job[0].m;
+    for (int j = 0; j < js.njobs; ++j) {
+        const Job<R>& J = js.job[j];
+        if (J.d != 3 || J.m != m || J.mode == INFFT_MODE_BOPT || J.T != SPREAD3D_T || J.T <= m) return false;
+    }
+    // the register-held cells fit without spilling up to m = 6 (float) / m = 5 (double)
+    if (m < 1 || m > (sizeof(R) == 4 ? 6 : 5)) return false;
+    *m_out = m;
+    return true;
+}
+
+template <class R>
+static infft_status launch_spread3d(JobSet<R>& js, cudaStream_t st, int m) {
+    switch (m) {
+        case 1: return launch_spread3d_m<R, 1>(js, st);
+        case 2: return launch_spread3d_m<R, 2>(js, st);
+        case 3: return launch_spread3d_m<R, 3>(js, st);
+        case 4: return launch_spread3d_m<R, 4>(js, st);
+        case 5: return launch_spread3d_m<R, 5>(js, st);
+        default: return launch_spread3d_m<R, 6>(js, st);
+    }
+}
+
+// pruned FFT passes with deconvolution, common to every spreading variant
+template <class R, int D>
+static infft_status launch_fft_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* ev) {
+    int maxMs = 0;
+    for (int j = 0; j < js.njobs; ++j) maxMs = std::max(maxMs, js.job[j].Ms);
+    const size_t fsmem = (size_t)js.L * (maxMs + maxMs / 16) * sizeof(cx<R>);
+    INFFT_CUDA(cudaFuncSetAttribute(k_fft<R, D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
+    for (int p = 0; p < D; ++p) {
+        k_fft<R, D, false><<<js.pre_fft[p][js.njobs], 256, fsmem, st>>>(js, p);
+        INFFT_LAUNCHED();
+        if (ev) INFFT_CUDA(cudaEventRecord(ev[3 + p], st));
+    }
+    return INFFT_OK;
+}
+
 template <class R, int D>
 static infft_status launch_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* ev) {
     fill_prefixes(js, D, false);
@@ -661,16 +1021,21 @@ static infft_status launch_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* 
         k_merge2d<R><<<js.pre_merge[js.njobs], 256, 0, st>>>(js);
         INFFT_LAUNCHED();
         if (ev) INFFT_CUDA(cudaEventRecord(ev[2], st));
-        int maxMs = 0;
-        for (int j = 0; j < js.njobs; ++j) maxMs = std::max(maxMs, js.job[j].Ms);
-        const size_t fsmem = (size_t)js.L * (maxMs + maxMs / 16) * sizeof(cx<R>);
-        INFFT_CUDA(cudaFuncSetAttribute(k_fft<R, D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
-        for (int p = 0; p < D; ++p) {
-            k_fft<R, D, false><<<js.pre_fft[p][js.njobs], 256, fsmem, st>>>(js, p);
-            INFFT_LAUNCHED();
-            if (ev) INFFT_CUDA(cudaEventRecord(ev[3 + p], st));
+        return launch_fft_adjoint<R, D>(js, st, ev);
+    }
+    int m3 = 0;
+    if (D == 3 && spread3d_eligible(js, &m3)) {
+        INFFT_TRY(launch_spread3d<R>(js, st, m3));
+        if (ev) INFFT_CUDA(cudaEventRecord(ev[1], st));
+        js.pre_merge[0] = 0;
+        for (int j = 0; j < js.njobs; ++j) {
+            const int nt = js.job[j].ntile;
+            js.pre_merge[j + 1] = js.pre_merge[j] + nt * nt * nt;
         }
-        return INFFT_OK;
+        k_merge3d<R><<<js.pre_merge[js.njobs], 256, 0, st>>>(js);
+        INFFT_LAUNCHED();
+        if (ev) INFFT_CUDA(cudaEventRecord(ev[2], st));
+        return launch_fft_adjoint<R, D>(js, st, ev);
     }
     const size_t spw = spread_smem_per_warp(js, D);
     const size_t smem_cap = 200 * 1024;
@@ -691,16 +1056,58 @@ static infft_status launch_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* 
     k_merge<R, D><<<js.pre_merge[js.njobs], 256, 0, st>>>(js);
     INFFT_LAUNCHED();
     if (ev) INFFT_CUDA(cudaEventRecord(ev[2], st));
-    int maxMs = 0;
-    for (int j = 0; j < js.njobs; ++j) maxMs = std::max(maxMs, js.job[j].Ms);
-    const size_t fsmem = (size_t)js.L * (maxMs + maxMs / 16) * sizeof(cx<R>);
-    INFFT_CUDA(cudaFuncSetAttribute(k_fft<R, D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
-    for (int p = 0; p < D; ++p) {
-        k_fft<R, D, false><<<js.pre_fft[p][js.njobs], 256, fsmem, st>>>(js, p);
-        INFFT_LAUNCHED();
-        if (ev) INFFT_CUDA(cudaEventRecord(ev[3 + p], st));
+    return launch_fft_adjoint<R, D>(js, st, ev);
+}
+
+template <class R, int D, int MM>
+static infft_status launch_interp_t(JobSet<R>& js, cudaStream_t st) {
+    int P = 0;
+    for (int j = 0; j < js.njobs; ++j) P = std::max(P, js.job[j].P);
+    const size_t cells = D == 3 ? (size_t)P * P * P : (size_t)P * P;
+    size_t spw = ((cells + 1) & ~(size_t)1) * sizeof(cx<R>) + (WPOLY_DEG + 1) * wpoly_stride(2 * MM + 1) * sizeof(float);
+    spw = (spw + 15) & ~(size_t)15;
+    const size_t smem_cap = 200 * 1024;
+    if (spw > smem_cap) {
+        set_error("padded tile needs %zu bytes of shared memory", spw);
+        return INFFT_EUNSUPPORTED;
     }
+    js.smem_per_warp = (int)spw;
+    js.wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (64 * 1024) / spw));
+    const int nitems = js.pre_items[js.njobs];
+    if (nitems == 0) return INFFT_OK;
+    const size_t smem = spw * js.wpb;
+    INFFT_CUDA(cudaFuncSetAttribute(k_interp_t<R, D, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_interp_t<R, D, MM><<<(nitems + js.wpb - 1) / js.wpb, 32 * js.wpb, smem, st>>>(js);
+    INFFT_LAUNCHED();
     return INFFT_OK;
+}
+
+// interpolation with a fixed m for d = 2, 3 (all jobs the same m, tile edge a power of two)
+template <class R, int D>
+static bool interp_t_eligible(const JobSet<R>& js, int* m_out) {
+    if (D < 2 || js.njobs < 1) return false;
+    const int m = js.job[0].m;
+    for (int j = 0; j < js.njobs; ++j) {
+        const Job<R>& J = js.job[j];
+        if (J.m != m || (J.T & (J.T - 1)) != 0 || (J.Ms & (J.Ms - 1)) != 0) return false;
+    }
+    if (m < 1 || m > 8) return false;
+    *m_out = m;
+    return true;
+}
+
+template <class R, int D>
+static infft_status launch_interp(JobSet<R>& js, cudaStream_t st, int m) {
+    switch (m) {
+        case 1: return launch_interp_t<R, D, 1>(js, st);
+        case 2: return launch_interp_t<R, D, 2>(js, st);
+        case 3: return launch_interp_t<R, D, 3>(js, st);
+        case 4: return launch_interp_t<R, D, 4>(js, st);
+        case 5: return launch_interp_t<R, D, 5>(js, st);
+        case 6: return launch_interp_t<R, D, 6>(js, st);
+        case 7: return launch_interp_t<R, D, 7>(js, st);
+        default: return launch_interp_t<R, D, 8>(js, st);
+    }
 }
 
 template <class R, int D>
@@ -713,6 +1120,10 @@ static infft_status launch_forward(JobSet<R>& js, cudaStream_t st) {
     for (int p = 0; p < D; ++p) {
         k_fft<R, D, true><<<js.pre_fft[p][js.njobs], 256, fsmem, st>>>(js, p);
         INFFT_LAUNCHED();
+    }
+    if constexpr (D >= 2) {
+        int mi = 0;
+        if (interp_t_eligible<R, D>(js, &mi)) return launch_interp<R, D>(js, st, mi);
     }
     size_t spw = 0;
     for (int j = 0; j < js.njobs; ++j) {

@@ -32,12 +32,22 @@ CASES = [  # d, M, N, sigma, m, generator
     (2, 8, 50, 2.0, 3, "random"),
     (3, 16, 2000, 2.0, 3, "random"),
     (3, 8, 700, 2.0, 2, "random"),
+    (3, 16, 2500, 2.0, 4, "random"),
+    (3, 16, 2500, 2.0, 5, "random"),
+    (3, 8, 4000, 2.0, 3, "clustered"),
+    (2, 32, 3000, 2.0, 4, "clustered"),
 ]
 
 
 def points(d, N, gen, seed):
     if gen == "jitter":
         return inputs.jittered_1d(N, seed)
+    if gen == "clustered":   # many points per base cell, some exactly repeated
+        g = inputs.rng(seed)
+        centres = g.uniform(-0.5, 0.5, size=(7, d))
+        x = centres[g.integers(0, 7, size=N)] + g.uniform(-1e-3, 1e-3, size=(N, d))
+        x[: N // 4] = centres[0]
+        return x
     if gen == "polar":
         n = int(np.sqrt(N))
         return inputs.polar(n, n)
@@ -70,7 +80,7 @@ def test_forward_fp64_matches_oracle_algorithm(case):
 
 
 @pytest.mark.parametrize("d,M,N,m", [(1, 64, 256, 6), (2, 64, 9001, 6), (2, 64, 9001, 4), (2, 128, 20000, 4),
-                                     (3, 16, 3000, 4)])
+                                     (3, 16, 3000, 4), (3, 16, 3000, 6), (3, 32, 30000, 4)])
 def test_fp32_within_1e5_of_exact_sums(d, M, N, m):
     L, torch = lib_or_skip()
     x = inputs.random_points(N, d, 5)
