@@ -361,7 +361,8 @@ static infft_status build_plan(infft_plan_s* p, const double* x_in, cudaStream_t
     std::vector<int> cs(nkeys + 1);
     INFFT_CUDA(cudaMemcpyAsync(cs.data(), count, (size_t)(nkeys + 1) * 4, cudaMemcpyDeviceToHost, st));
     INFFT_CUDA(cudaStreamSynchronize(st));
-    const int cap = 512;
+    // d = 1: short items so that a few hundred points still spread on several warps
+    const int cap = d == 1 ? 32 : 512;
     std::vector<int4> items;
     std::vector<int> tile_items(ntiles + 1, 0);
     for (int tl = 0; tl < ntiles; ++tl) {

@@ -49,8 +49,9 @@ class PointSet:
     key: Any
     d: int
     M: int
-    x: Any                   # N x d float64 (host)
+    x: Any                   # N x d float64 (host), or a callable returning it
     precision: str = "fp32"
+    N: int = 0               # number of points (needed when x is a callable)
 
 
 class Backend:
@@ -65,7 +66,8 @@ class Backend:
         L.load()
 
     def build_plan(self, ps: PointSet, stream):
-        p = self.L.Plan(ps.x, ps.M, self.sigma, self.m, ps.precision, stream=stream.cuda_stream)
+        x = ps.x() if callable(ps.x) else ps.x
+        p = self.L.Plan(x, ps.M, self.sigma, self.m, ps.precision, stream=stream.cuda_stream)
         p.weights(max_iter=self.weights_iters, rel_tol=1e-12, stream=stream.cuda_stream)
         return p
 
@@ -73,7 +75,7 @@ class Backend:
         return plan.device_bytes
 
     def estimate_bytes(self, ps: PointSet) -> int:
-        n = ps.x.shape[0]
+        n = ps.N if ps.N else ps.x.shape[0]
         grid = (2 * ps.M) ** ps.d
         cg = 16 * ((4 * ps.M) ** ps.d) * 8   # float64 grids and scratch of the degree-2M solve
         return 120 * n + 40 * grid + cg
@@ -117,6 +119,7 @@ class Server:
         self.plan_meta: Dict[Any, PointSet] = {}
         self.plan_used: Dict[Any, float] = {}
         self.plan_size: Dict[Any, int] = {}
+        self.pinned: set = set()           # point sets never evicted
         self.plan_refs: Dict[Any, int] = collections.Counter()   # requests queued or in flight
         self.resident_bytes = 0        # plans on the device
         self.reserved: Dict[Any, int] = {}   # estimates of plans being built
@@ -126,6 +129,8 @@ class Server:
         self.completed: List[Request] = []
         self.stats = collections.Counter()
         self._retry: List[PointSet] = []
+        self._deferred_keys: set = set()
+        self.build_times: List[tuple] = []    # (key, seconds) of every plan built
         self._lock = threading.Lock()
         self._work: queue.Queue = queue.Queue()
         self._ready: queue.Queue = queue.Queue()
@@ -134,8 +139,10 @@ class Server:
         self._worker.start()
 
     # ---- admission of point sets ------------------------------------------------------
-    def register(self, ps: PointSet):
+    def register(self, ps: PointSet, pin: bool = False):
         self.plan_meta[ps.key] = ps
+        if pin:
+            self.pinned.add(ps.key)
 
     def _precompute_loop(self):
         while True:
@@ -143,7 +150,9 @@ class Server:
             if ps is None:
                 return
             try:
+                t0 = time.perf_counter()
                 plan = self.be.build_plan(ps, self._pstream)
+                self.build_times.append((ps.key, time.perf_counter() - t0))
                 self._ready.put((ps.key, plan, None))
             except Exception as e:  # surfaced to the requests of this key
                 self._ready.put((ps.key, None, e))
@@ -156,7 +165,7 @@ class Server:
                 return False
             return self.be.free_bytes() - sum(self.reserved.values()) > need
         while not fits():
-            idle = [k for k in self.plans if self.plan_refs[k] == 0]
+            idle = [k for k in self.plans if self.plan_refs[k] == 0 and k not in self.pinned]
             if not idle:
                 return False
             victim = min(idle, key=lambda k: self.plan_used[k])
@@ -187,7 +196,9 @@ class Server:
         elif not self.plans and not self.reserved:
             raise MemoryError(f"point set {ps.key!r} needs ~{need} bytes, more than the budget")
         else:
-            self.stats["admit_deferred"] += 1
+            if ps.key not in self._deferred_keys:
+                self._deferred_keys.add(ps.key)
+                self.stats["admit_deferred"] += 1
             self._retry.append(ps)
 
     # ---- the loop ------------------------------------------------------------------------
@@ -286,14 +297,27 @@ class Server:
         self._work.put(None)
         self._worker.join(timeout=5)
 
+    def abort(self, timeout: float = 60.0):
+        """Drop queued plan builds, wait for the one in progress and stop the worker."""
+        while True:
+            try:
+                self._work.get_nowait()
+            except queue.Empty:
+                break
+        self._work.put(None)
+        self._worker.join(timeout=timeout)
+
 
 def run_poisson(server: Server, requests: List[Request], rate: float, seed: int = 0,
-                clock: Callable[[], float] = time.perf_counter) -> List[Request]:
+                clock: Callable[[], float] = time.perf_counter, time_limit: Optional[float] = None,
+                on_arrival: Optional[Callable[[Request], None]] = None) -> List[Request]:
     """Feed `requests` at Poisson arrival times of mean rate `rate` (per second) while
-    stepping the server; returns the completed requests."""
+    stepping the server; returns the completed requests.  With `time_limit` (seconds)
+    the run stops there: later arrivals are not submitted and unfinished requests stay
+    incomplete.  `on_arrival` runs for each request just before it is submitted."""
     import random
     rng = random.Random(seed)
-    t = clock()
+    t = t_start = clock()
     arrivals = []
     for r in requests:
         t += rng.expovariate(rate)
@@ -301,8 +325,12 @@ def run_poisson(server: Server, requests: List[Request], rate: float, seed: int 
     i = 0
     while i < len(arrivals) or server.step() > 0:
         now = clock()
+        if time_limit is not None and now - t_start > time_limit:
+            break
         while i < len(arrivals) and arrivals[i][0] <= now:
             arrivals[i][1].t_arrive = arrivals[i][0]
+            if on_arrival is not None:
+                on_arrival(arrivals[i][1])
             server.submit(arrivals[i][1])
             i += 1
         server.step()

@@ -164,3 +164,19 @@ def test_over_budget_point_set_is_an_error():
     else:
         raise AssertionError("expected MemoryError")
     s.close()
+
+
+def test_pinned_point_sets_are_never_evicted():
+    be = FakeBackend(latency=1)
+    s = Server(be, mem_budget=250, max_batch=4, streams=2)
+    all_sets = sets(5)
+    s.register(all_sets[0], pin=True)
+    for ps in all_sets[1:]:
+        s.register(ps)
+    for i in range(12):
+        s.submit(Request(rid=i, key=i % 5, f=i))
+        s.drain(timeout=30)
+    assert len(s.completed) == 12
+    assert 0 not in be.released and 0 in s.plans
+    assert s.stats["evicted"] > 0
+    s.close()
