@@ -9,6 +9,7 @@
 
 #include "internal.h"
 #include "jobset.cuh"
+#include "spread.cuh"
 
 namespace infft {
 
@@ -103,315 +104,6 @@ __global__ void __launch_bounds__(128) k_spread(const __grid_constant__ JobSet<R
     }
     cx<R>* dst = J.padded + (size_t)it * cells;
     for (int e = lane; e < cells; e += 32) dst[e] = pad[e];
-}
-
-// ---------------------------------------------------------------------------------------
-// Two-dimensional spreading with the accumulators in registers.  One warp per work
-// item; lane l owns column l of the item's P x P padded tile (P = T + 2m + 1 <= 32).
-// The item's points are sorted by base row, so the rows a point can touch,
-// [oy, oy + 2m] (padded coordinates; one more row for B_opt slots), only move down:
-// each lane keeps those rows of its column in registers, adds the point's taps
-// (coefficient c_j psi_y[k] broadcast, times psi_x of its column), and when the next
-// point starts lower it stores the rows that no later point can reach.  Every padded
-// cell is stored exactly once, no shared-memory read-modify-write, no atomics.
-// Window values are computed once per point while staging 32 points per warp.
-template <class R, int MM, bool BOPT>
-__global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet<R> js) {
-    constexpr int W = 2 * MM + 1;              // window taps per axis
-    constexpr int WE = W + 1;                  // even stride of the staged rows (16-byte loads)
-    constexpr int WR = BOPT ? W + 1 : W;       // rows held in registers
-    constexpr bool F32 = sizeof(R) == 4;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gitem = blockIdx.x * js.wpb + warp;
-    if (gitem >= js.pre_items[js.njobs]) return;
-    const int jb = find_job(js.pre_items, js.njobs, gitem);
-    const Job<R>& J = js.job[jb];
-    const int it = gitem - js.pre_items[jb];
-    const int4 item = J.items[it];
-    const int P = J.P, Ms = J.Ms, T = J.T;
-
-    unsigned char* base = smem_raw + (size_t)warp * js.smem_per_warp;
-    cx<R>* cy = reinterpret_cast<cx<R>*>(base);            // [32][WE] c_j psi_y (window mode)
-    R* psx = reinterpret_cast<R*>(cy + 32 * WE);            // [32][WE] psi_x
-    int* meta = reinterpret_cast<int*>(psx + 32 * WE);      // [32][3]  oy, ox, sorted index
-    cx<R>* cst = reinterpret_cast<cx<R>*>(meta + 96);       // [32]     c_j (B_opt mode)
-    float* poly = reinterpret_cast<float*>(cst + 32);       // [(WPOLY_DEG+1) * WP] window polynomial (16-byte rows)
-    const bool use_poly = F32 && !BOPT && J.wpoly != nullptr;
-    if (use_poly) {
-        for (int e = lane; e < (WPOLY_DEG + 1) * wpoly_stride(W); e += 32) poly[e] = J.wpoly[e];
-    }
-
-    const int ty = item.x / J.ntile, tx = item.x % J.ntile;
-    using V2 = typename std::conditional<F32, float2, double2>::type;
-    V2 acc[WR];  // (re, im) of the rows r0 .. r0 + WR - 1 of this lane's column
-#pragma unroll
-    for (int k = 0; k < WR; ++k) { acc[k].x = R(0); acc[k].y = R(0); }
-    int r0 = 0;  // padded row held in acc[0]
-    cx<R>* dst = J.padded + (size_t)it * P * P;
-    const bool col_ok = lane < P;
-    const int logMs = 31 - __clz(Ms);
-
-    for (int c0 = 0; c0 < item.z; c0 += 32) {
-        const int np = min(32, item.z - c0);
-        __syncwarp();
-        if (lane < np) {
-            const int i = item.y + c0 + lane;
-            const int j = __ldg(J.perm + i);
-            cx<R> fv = J.in[j];
-            if (J.mode == INFFT_MODE_DCF) fv = mul(J.w[i], fv);
-            const uint32_t cl = __ldg(J.cell + i);
-            const int cxl = (int)(cl & (uint32_t)(Ms - 1)), cyl = (int)(cl >> logMs);
-            meta[lane * 3 + 0] = cyl - ty * T;
-            meta[lane * 3 + 1] = cxl - tx * T;
-            meta[lane * 3 + 2] = i;
-            if (BOPT) {
-                cst[lane] = fv;
-            } else {
-                const R uy = J.u[(size_t)i * 2 + 0], ux = J.u[(size_t)i * 2 + 1];
-                R wy[W], wx[W];
-                bool done = false;
-                if constexpr (F32) {
-                    if (use_poly) {
-                        poly_taps2<W>(poly, uy, ux, wy, wx);
-                        done = true;
-                    }
-                }
-                if (!done) {
-#pragma unroll
-                    for (int s = 0; s < W; ++s) {
-                        wy[s] = tap_weight<R>(J.window, uy, s, MM, J.inv_m, J.beta);
-                        wx[s] = tap_weight<R>(J.window, ux, s, MM, J.inv_m, J.beta);
-                    }
-                }
-#pragma unroll
-                for (int s = 0; s < W; ++s) {
-                    cy[lane * WE + s] = scale(fv, wy[s]);
-                    psx[lane * WE + s] = wx[s];
-                }
-                cy[lane * WE + W] = mk<R>(0, 0);
-            }
-        }
-        __syncwarp();
-        for (int p = 0; p < np; ++p) {
-            const int oy = meta[p * 3 + 0], ox = meta[p * 3 + 1];
-            // store the rows above oy: no later point reaches them
-            while (r0 < oy) {
-                if (col_ok) dst[(size_t)r0 * P + lane] = mk<R>(acc[0].x, acc[0].y);
-#pragma unroll
-                for (int k = 0; k < WR - 1; ++k) acc[k] = acc[k + 1];
-                acc[WR - 1].x = R(0);
-                acc[WR - 1].y = R(0);
-                ++r0;
-            }
-            const int sx = lane - ox;
-            if (BOPT) {
-                constexpr int S = W + 1;
-                if (sx >= 0 && sx < S) {
-                    const int i = meta[p * 3 + 2];
-                    const cx<R> cv = cst[p];
-                    const cx<R>* cf = J.coef + (size_t)i * S * S + sx;
-#pragma unroll
-                    for (int k = 0; k < S; ++k) {
-                        const cx<R> b = cf[k * S];
-                        acc[k].x += b.re * cv.re + b.im * cv.im;   // conj(b) f
-                        acc[k].y += b.re * cv.im - b.im * cv.re;
-                    }
-                }
-            } else {
-                const bool in = (sx >= 0) && (sx < W);
-                const R wx = in ? psx[p * WE + (in ? sx : 0)] : R(0);
-                const cx<R>* cp = cy + p * WE;
-                if constexpr (F32) {
-                    // two complex coefficients per 16-byte broadcast load, one packed
-                    // two-wide FMA per row
-                    const float4* cp4 = reinterpret_cast<const float4*>(cp);
-                    const float2 ww = make_float2(wx, wx);
-#pragma unroll
-                    for (int k2 = 0; k2 < WE / 2; ++k2) {
-                        const float4 c = cp4[k2];
-                        acc[2 * k2] = __ffma2_rn(make_float2(c.x, c.y), ww, acc[2 * k2]);
-                        if (2 * k2 + 1 < W) acc[2 * k2 + 1] = __ffma2_rn(make_float2(c.z, c.w), ww, acc[2 * k2 + 1]);
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < W; ++k) {
-                        const cx<R> c = cp[k];
-                        acc[k].x += c.re * wx;
-                        acc[k].y += c.im * wx;
-                    }
-                }
-            }
-        }
-    }
-    // remaining rows (including rows no point reached)
-    while (r0 < P) {
-        if (col_ok) dst[(size_t)r0 * P + lane] = mk<R>(acc[0].x, acc[0].y);
-#pragma unroll
-        for (int k = 0; k < WR - 1; ++k) acc[k] = acc[k + 1];
-        acc[WR - 1].x = R(0);
-        acc[WR - 1].y = R(0);
-        ++r0;
-    }
-}
-
-// ---------------------------------------------------------------------------------------
-// Three-dimensional spreading (window modes), tiles of 8^3 cells.  One warp per work item,
-// the item's padded tile of P^3 cells (P = 8 + 2m + 1) in shared memory.  Lane l takes
-// the (z, x) tap pairs q = l + 32 r of a point (W^2 pairs, ceil(W^2 / 32) rounds) and
-// holds the W cells of each pair along y in registers, adding (c_j psi_y) psi_z psi_x.
-// The items' points are sorted by base cell: while consecutive points share their base
-// cell the registers keep accumulating; when it changes, the lanes store their cells,
-// meet at a __syncwarp and load the cells of the new base.  Each cell is summed in the
-// item's point order (deterministic, no atomics) and shared memory is touched once per
-// base cell rather than once per point.
-// The z-planes of the shared tile are PZ >= P^2 cells apart with PZ = W (mod 16), so the
-// cells of 16 consecutive pairs, at q + const (mod 16) in 8-byte units, fall into
-// distinct bank pairs: no bank conflicts.  The tile is written out densely (P^3).
-__host__ __device__ constexpr int spread3d_plane(int P, int W) { return P * P + (((W - P * P) % 16) + 16) % 16; }
-constexpr int SPREAD3D_T = 8;
-
-template <class R, int MM>
-__global__ void __launch_bounds__(64) k_spread3d(const __grid_constant__ JobSet<R> js) {
-    constexpr int W = 2 * MM + 1;
-    constexpr int WE = W + 1;                  // even stride of the staged rows
-    constexpr int NR = (W * W + 31) / 32;      // rounds over the (z, x) pairs
-    constexpr int T = SPREAD3D_T;
-    constexpr int P = T + 2 * MM + 1, P2 = P * P;
-    constexpr int PZ = spread3d_plane(P, W), SC = P * PZ;
-    constexpr bool F32 = sizeof(R) == 4;
-    using V2 = typename std::conditional<F32, float2, double2>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gitem = blockIdx.x * js.wpb + warp;
-    if (gitem >= js.pre_items[js.njobs]) return;
-    const int jb = find_job(js.pre_items, js.njobs, gitem);
-    const Job<R>& J = js.job[jb];
-    const int it = gitem - js.pre_items[jb];
-    const int4 item = J.items[it];
-    const int Ms = J.Ms, nt = J.ntile;
-
-    unsigned char* base = smem_raw + (size_t)warp * js.smem_per_warp;
-    V2* pad = reinterpret_cast<V2*>(base);                             // [P][PZ]
-    V2* cyv = pad + ((SC + 1) & ~1);                                   // [32][WE] c_j psi_y
-    R* psz = reinterpret_cast<R*>(cyv + 32 * WE);                      // [32][WE]
-    R* psx = psz + 32 * WE;                                            // [32][WE]
-    int* meta = reinterpret_cast<int*>(psx + 32 * WE);                 // [32] base cell in the shared tile
-    float* poly = reinterpret_cast<float*>(meta + 32);                 // window polynomial (float32 plans)
-    const bool use_poly = F32 && J.wpoly != nullptr;
-    if (use_poly) {
-        for (int e = lane; e < (WPOLY_DEG + 1) * wpoly_stride(W); e += 32) poly[e] = J.wpoly[e];
-    }
-    for (int e = lane; e < SC; e += 32) { pad[e].x = R(0); pad[e].y = R(0); }
-
-    const int tz = item.x / (nt * nt), ty = (item.x / nt) % nt, tx = item.x % nt;
-    const int logMs = 31 - __clz(Ms);
-    int off[NR], sz[NR], sx[NR];
-    bool ok[NR];
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-        const int q = lane + 32 * r;
-        ok[r] = q < W * W;
-        sz[r] = ok[r] ? q / W : 0;
-        sx[r] = ok[r] ? q % W : 0;
-        off[r] = sz[r] * PZ + sx[r];
-    }
-    V2 v[NR][W];
-#pragma unroll
-    for (int r = 0; r < NR; ++r)
-#pragma unroll
-        for (int s = 0; s < W; ++s) { v[r][s].x = R(0); v[r][s].y = R(0); }
-    int cur = -1;
-
-    for (int c0 = 0; c0 < item.z; c0 += 32) {
-        const int np = min(32, item.z - c0);
-        __syncwarp();
-        if (lane < np) {
-            const int i = item.y + c0 + lane;
-            const int j = __ldg(J.perm + i);
-            cx<R> fv = J.in[j];
-            if (J.mode == INFFT_MODE_DCF) fv = mul(J.w[i], fv);
-            const uint32_t cl = __ldg(J.cell + i);
-            const int cxl = (int)(cl & (uint32_t)(Ms - 1));
-            const int cyl = (int)((cl >> logMs) & (uint32_t)(Ms - 1));
-            const int czl = (int)(cl >> (2 * logMs));
-            meta[lane] = (czl - tz * T) * PZ + (cyl - ty * T) * P + (cxl - tx * T);
-            const R uz = J.u[(size_t)i * 3 + 0], uy = J.u[(size_t)i * 3 + 1], ux = J.u[(size_t)i * 3 + 2];
-            R wz[W], wy[W], wx[W];
-            bool done = false;
-            if constexpr (F32) {
-                if (use_poly) {
-                    poly_taps2<W>(poly, uz, uy, wz, wy);
-                    poly_taps<W>(poly, ux, wx);
-                    done = true;
-                }
-            }
-            if (!done) {
-#pragma unroll
-                for (int s = 0; s < W; ++s) {
-                    wz[s] = tap_weight<R>(J.window, uz, s, MM, J.inv_m, J.beta);
-                    wy[s] = tap_weight<R>(J.window, uy, s, MM, J.inv_m, J.beta);
-                    wx[s] = tap_weight<R>(J.window, ux, s, MM, J.inv_m, J.beta);
-                }
-            }
-#pragma unroll
-            for (int s = 0; s < W; ++s) {
-                cyv[lane * WE + s].x = fv.re * wy[s];
-                cyv[lane * WE + s].y = fv.im * wy[s];
-                psz[lane * WE + s] = wz[s];
-                psx[lane * WE + s] = wx[s];
-            }
-        }
-        __syncwarp();
-        for (int p = 0; p < np; ++p) {
-            const int b0 = meta[p];
-            if (b0 != cur) {   // uniform across the warp
-                if (cur >= 0) {
-#pragma unroll
-                    for (int r = 0; r < NR; ++r)
-                        if (ok[r]) {
-#pragma unroll
-                            for (int s = 0; s < W; ++s) pad[cur + off[r] + s * P] = v[r][s];
-                        }
-                }
-                __syncwarp();
-#pragma unroll
-                for (int r = 0; r < NR; ++r)
-                    if (ok[r]) {
-#pragma unroll
-                        for (int s = 0; s < W; ++s) v[r][s] = pad[b0 + off[r] + s * P];
-                    }
-                cur = b0;
-            }
-            V2 c[W];
-#pragma unroll
-            for (int s = 0; s < W; ++s) c[s] = cyv[p * WE + s];
-#pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                const R w = psz[p * WE + sz[r]] * psx[p * WE + sx[r]];
-                if constexpr (F32) {
-                    const float2 ww = make_float2(w, w);
-#pragma unroll
-                    for (int s = 0; s < W; ++s) v[r][s] = __ffma2_rn(c[s], ww, v[r][s]);
-                } else {
-#pragma unroll
-                    for (int s = 0; s < W; ++s) { v[r][s].x += c[s].x * w; v[r][s].y += c[s].y * w; }
-                }
-            }
-        }
-    }
-    if (cur >= 0) {
-#pragma unroll
-        for (int r = 0; r < NR; ++r)
-            if (ok[r]) {
-#pragma unroll
-                for (int s = 0; s < W; ++s) pad[cur + off[r] + s * P] = v[r][s];
-            }
-    }
-    __syncwarp();
-    V2* dst = reinterpret_cast<V2*>(J.padded) + (size_t)it * P2 * P;
-    for (int z = 0; z < P; ++z)
-        for (int e = lane; e < P2; e += 32) dst[(size_t)z * P2 + e] = pad[z * PZ + e];
 }
 
 template <class R, int D>
@@ -750,100 +442,6 @@ __global__ void __launch_bounds__(128) k_interp(const __grid_constant__ JobSet<R
 }
 
 // ---------------------------------------------------------------------------------------
-// Interpolation for d = 2, 3 with a fixed m: one warp per work item; the warp gathers the
-// padded tile of the grid around its tile into shared memory, then every lane sums the
-// W^d taps of one point in separable order (x innermost, then y, then z) and writes f_j
-// in the caller's order.  Window values come from the float32 polynomial or the exact
-// window (float64 plans).
-template <class R, int D, int MM>
-__global__ void __launch_bounds__(128) k_interp_t(const __grid_constant__ JobSet<R> js) {
-    constexpr int W = 2 * MM + 1;
-    constexpr bool F32 = sizeof(R) == 4;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gitem = blockIdx.x * js.wpb + warp;
-    if (gitem >= js.pre_items[js.njobs]) return;
-    const int jb = find_job(js.pre_items, js.njobs, gitem);
-    const Job<R>& J = js.job[jb];
-    const int4 item = J.items[gitem - js.pre_items[jb]];
-    const int P = J.P, m = J.m, Ms = J.Ms, T = J.T, nt = J.ntile;
-    const int cells = D == 3 ? P * P * P : P * P;
-    unsigned char* base = smem_raw + (size_t)warp * js.smem_per_warp;
-    cx<R>* pad = reinterpret_cast<cx<R>*>(base);
-    float* poly = reinterpret_cast<float*>(pad + ((cells + 1) & ~1));
-    const bool use_poly = F32 && J.wpoly != nullptr;
-    if (use_poly) {
-        for (int e = lane; e < (WPOLY_DEG + 1) * wpoly_stride(W); e += 32) poly[e] = J.wpoly[e];
-    }
-    int tz = 0, ty, tx;
-    if (D == 3) { tz = item.x / (nt * nt); ty = (item.x / nt) % nt; tx = item.x % nt; }
-    else { ty = item.x / nt; tx = item.x % nt; }
-    const int Mmask = Ms - 1;  // Ms is a power of two
-    for (int e = lane; e < cells; e += 32) {
-        const int ox = e % P, r1 = e / P;
-        const int oy = r1 % P, oz = r1 / P;
-        const int gx = (tx * T - m + ox) & Mmask, gy = (ty * T - m + oy) & Mmask;
-        size_t g = (size_t)gy * Ms + gx;
-        if (D == 3) g += (size_t)((tz * T - m + oz) & Mmask) * Ms * Ms;
-        pad[e] = J.grid[g];
-    }
-    __syncwarp();
-    const int logMs = 31 - __clz(Ms);
-    for (int c0 = 0; c0 < item.z; c0 += 32) {
-        const int np = min(32, item.z - c0);
-        if (lane >= np) continue;
-        const int i = item.y + c0 + lane;
-        const uint32_t cl = __ldg(J.cell + i);
-        const int ox = (int)(cl & (uint32_t)Mmask) - tx * T;
-        const int oy = (int)((cl >> logMs) & (uint32_t)Mmask) - ty * T;
-        const int oz = D == 3 ? (int)(cl >> (2 * logMs)) - tz * T : 0;
-        R wz[W], wy[W], wx[W];
-        const R uy = J.u[(size_t)i * D + D - 2], ux = J.u[(size_t)i * D + D - 1];
-        const R uz = D == 3 ? J.u[(size_t)i * D] : R(0);
-        bool done = false;
-        if constexpr (F32) {
-            if (use_poly) {
-                poly_taps2<W>(poly, uy, ux, wy, wx);
-                if (D == 3) poly_taps<W>(poly, uz, wz);
-                done = true;
-            }
-        }
-        if (!done) {
-#pragma unroll
-            for (int s = 0; s < W; ++s) {
-                wy[s] = tap_weight<R>(J.window, uy, s, MM, J.inv_m, J.beta);
-                wx[s] = tap_weight<R>(J.window, ux, s, MM, J.inv_m, J.beta);
-                if (D == 3) wz[s] = tap_weight<R>(J.window, uz, s, MM, J.inv_m, J.beta);
-            }
-        }
-        cx<R> acc = mk<R>(0, 0);
-        const int NZ = D == 3 ? W : 1;
-#pragma unroll 1
-        for (int sz = 0; sz < NZ; ++sz) {
-            cx<R> accy = mk<R>(0, 0);
-            const cx<R>* plane = pad + (size_t)(oz + sz) * P * P;
-#pragma unroll
-            for (int sy = 0; sy < W; ++sy) {
-                const cx<R>* row = plane + (oy + sy) * P + ox;
-                cx<R> t = mk<R>(0, 0);
-#pragma unroll
-                for (int sx = 0; sx < W; ++sx) {
-                    const cx<R> g = row[sx];
-                    t.re += wx[sx] * g.re;
-                    t.im += wx[sx] * g.im;
-                }
-                accy.re += wy[sy] * t.re;
-                accy.im += wy[sy] * t.im;
-            }
-            const R wzs = D == 3 ? wz[sz] : R(1);
-            acc.re += wzs * accy.re;
-            acc.im += wzs * accy.im;
-        }
-        J.out[__ldg(J.perm + i)] = acc;
-    }
-}
-
-// ---------------------------------------------------------------------------------------
 // host drivers
 
 static int pick_lines(int n, size_t elem) {
@@ -892,104 +490,6 @@ static size_t spread_smem_per_warp(const JobSet<R>& js, int D) {
     return mx;
 }
 
-// register-row spreading for d = 2 when every job has the same m (2..7) and P <= 32
-template <class R, int MM, bool BOPT>
-static infft_status launch_spread2d_m(JobSet<R>& js, cudaStream_t st) {
-    constexpr int W = 2 * MM + 1;
-    constexpr int WE = W + 1;
-    size_t spw = 32 * WE * sizeof(cx<R>) + 32 * WE * sizeof(R) + 96 * sizeof(int) + 32 * sizeof(cx<R>) +
-                 (WPOLY_DEG + 1) * wpoly_stride(W) * sizeof(float);
-    spw = (spw + 15) & ~(size_t)15;
-    js.smem_per_warp = (int)spw;
-    js.wpb = 4;
-    const int nitems = js.pre_items[js.njobs];
-    if (nitems == 0) return INFFT_OK;
-    const size_t smem = spw * js.wpb;
-    INFFT_CUDA(cudaFuncSetAttribute(k_spread2d<R, MM, BOPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_spread2d<R, MM, BOPT><<<(nitems + js.wpb - 1) / js.wpb, 32 * js.wpb, smem, st>>>(js);
-    INFFT_LAUNCHED();
-    return INFFT_OK;
-}
-
-template <class R, bool BOPT>
-static infft_status launch_spread2d(JobSet<R>& js, cudaStream_t st, int m) {
-    switch (m) {
-        case 2: return launch_spread2d_m<R, 2, BOPT>(js, st);
-        case 3: return launch_spread2d_m<R, 3, BOPT>(js, st);
-        case 4: return launch_spread2d_m<R, 4, BOPT>(js, st);
-        case 5: return launch_spread2d_m<R, 5, BOPT>(js, st);
-        case 6: return launch_spread2d_m<R, 6, BOPT>(js, st);
-        default: return launch_spread2d_m<R, 7, BOPT>(js, st);
-    }
-}
-
-template <class R>
-static bool spread2d_eligible(const JobSet<R>& js, int* m_out, bool* bopt_out) {
-    if (js.njobs < 1) return false;
-    const int m = js.job[0].m;
-    const bool bopt = js.job[0].mode == INFFT_MODE_BOPT;
-    for (int j = 0; j < js.njobs; ++j) {
-        const Job<R>& J = js.job[j];
-        if (J.d != 2 || J.m != m || (J.mode == INFFT_MODE_BOPT) != bopt || J.P > 32) return false;
-    }
-    if (m < 2 || m > 7) return false;
-    *m_out = m;
-    *bopt_out = bopt;
-    return true;
-}
-
-// three-dimensional spreading in window modes when every job has the same m (1..7)
-template <class R, int MM>
-static infft_status launch_spread3d_m(JobSet<R>& js, cudaStream_t st) {
-    constexpr int W = 2 * MM + 1;
-    constexpr int WE = W + 1;
-    constexpr int P = SPREAD3D_T + 2 * MM + 1;
-    const size_t cells = (size_t)P * spread3d_plane(P, W);
-    size_t spw = ((cells + 1) & ~(size_t)1) * sizeof(cx<R>) + 32 * WE * (sizeof(cx<R>) + 2 * sizeof(R)) +
-                 32 * sizeof(int) + (WPOLY_DEG + 1) * wpoly_stride(W) * sizeof(float);
-    spw = (spw + 15) & ~(size_t)15;
-    const size_t smem_cap = 200 * 1024;
-    if (spw > smem_cap) {
-        set_error("padded tile needs %zu bytes of shared memory", spw);
-        return INFFT_EUNSUPPORTED;
-    }
-    js.smem_per_warp = (int)spw;
-    js.wpb = spw > 48 * 1024 ? 1 : 2;
-    const int nitems = js.pre_items[js.njobs];
-    if (nitems == 0) return INFFT_OK;
-    const size_t smem = spw * js.wpb;
-    INFFT_CUDA(cudaFuncSetAttribute(k_spread3d<R, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_spread3d<R, MM><<<(nitems + js.wpb - 1) / js.wpb, 32 * js.wpb, smem, st>>>(js);
-    INFFT_LAUNCHED();
-    return INFFT_OK;
-}
-
-template <class R>
-static bool spread3d_eligible(const JobSet<R>& js, int* m_out) {
-    if (js.njobs < 1) return false;
-    const int m = js.job[0].m;
-    for (int j = 0; j < js.njobs; ++j) {
-        const Job<R>& J = js.job[j];
-        if (J.d != 3 || J.m != m || J.mode == INFFT_MODE_BOPT || J.T != SPREAD3D_T || J.T <= m) return false;
-    }
-    // the register-held cells fit without spilling up to m = 6 (float) / m = 5 (double)
-    if (m < 1 || m > (sizeof(R) == 4 ? 6 : 5)) return false;
-    *m_out = m;
-    return true;
-}
-
-template <class R>
-static infft_status launch_spread3d(JobSet<R>& js, cudaStream_t st, int m) {
-    switch (m) {
-        case 1: return launch_spread3d_m<R, 1>(js, st);
-        case 2: return launch_spread3d_m<R, 2>(js, st);
-        case 3: return launch_spread3d_m<R, 3>(js, st);
-        case 4: return launch_spread3d_m<R, 4>(js, st);
-        case 5: return launch_spread3d_m<R, 5>(js, st);
-        default: return launch_spread3d_m<R, 6>(js, st);
-    }
-}
-
 // pruned FFT passes with deconvolution, common to every spreading variant
 template <class R, int D>
 static infft_status launch_fft_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* ev) {
@@ -1009,11 +509,9 @@ template <class R, int D>
 static infft_status launch_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* ev) {
     fill_prefixes(js, D, false);
     if (ev) INFFT_CUDA(cudaEventRecord(ev[0], st));
-    int m2 = 0;
-    bool bopt2 = false;
-    if (D == 2 && spread2d_eligible(js, &m2, &bopt2)) {
-        const infft_status s2 = bopt2 ? launch_spread2d<R, true>(js, st, m2) : launch_spread2d<R, false>(js, st, m2);
-        if (s2 != INFFT_OK) return s2;
+    bool used = false;
+    if (D == 2) INFFT_TRY(spread2d_try<R>(js, st, &used));
+    if (used) {
         if (ev) INFFT_CUDA(cudaEventRecord(ev[1], st));
         // merge: one block per tile
         js.pre_merge[0] = 0;
@@ -1023,9 +521,8 @@ static infft_status launch_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* 
         if (ev) INFFT_CUDA(cudaEventRecord(ev[2], st));
         return launch_fft_adjoint<R, D>(js, st, ev);
     }
-    int m3 = 0;
-    if (D == 3 && spread3d_eligible(js, &m3)) {
-        INFFT_TRY(launch_spread3d<R>(js, st, m3));
+    if (D == 3) INFFT_TRY(spread3d_try<R>(js, st, &used));
+    if (used) {
         if (ev) INFFT_CUDA(cudaEventRecord(ev[1], st));
         js.pre_merge[0] = 0;
         for (int j = 0; j < js.njobs; ++j) {
@@ -1059,57 +556,6 @@ static infft_status launch_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* 
     return launch_fft_adjoint<R, D>(js, st, ev);
 }
 
-template <class R, int D, int MM>
-static infft_status launch_interp_t(JobSet<R>& js, cudaStream_t st) {
-    int P = 0;
-    for (int j = 0; j < js.njobs; ++j) P = std::max(P, js.job[j].P);
-    const size_t cells = D == 3 ? (size_t)P * P * P : (size_t)P * P;
-    size_t spw = ((cells + 1) & ~(size_t)1) * sizeof(cx<R>) + (WPOLY_DEG + 1) * wpoly_stride(2 * MM + 1) * sizeof(float);
-    spw = (spw + 15) & ~(size_t)15;
-    const size_t smem_cap = 200 * 1024;
-    if (spw > smem_cap) {
-        set_error("padded tile needs %zu bytes of shared memory", spw);
-        return INFFT_EUNSUPPORTED;
-    }
-    js.smem_per_warp = (int)spw;
-    js.wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (64 * 1024) / spw));
-    const int nitems = js.pre_items[js.njobs];
-    if (nitems == 0) return INFFT_OK;
-    const size_t smem = spw * js.wpb;
-    INFFT_CUDA(cudaFuncSetAttribute(k_interp_t<R, D, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_interp_t<R, D, MM><<<(nitems + js.wpb - 1) / js.wpb, 32 * js.wpb, smem, st>>>(js);
-    INFFT_LAUNCHED();
-    return INFFT_OK;
-}
-
-// interpolation with a fixed m for d = 2, 3 (all jobs the same m, tile edge a power of two)
-template <class R, int D>
-static bool interp_t_eligible(const JobSet<R>& js, int* m_out) {
-    if (D < 2 || js.njobs < 1) return false;
-    const int m = js.job[0].m;
-    for (int j = 0; j < js.njobs; ++j) {
-        const Job<R>& J = js.job[j];
-        if (J.m != m || (J.T & (J.T - 1)) != 0 || (J.Ms & (J.Ms - 1)) != 0) return false;
-    }
-    if (m < 1 || m > 8) return false;
-    *m_out = m;
-    return true;
-}
-
-template <class R, int D>
-static infft_status launch_interp(JobSet<R>& js, cudaStream_t st, int m) {
-    switch (m) {
-        case 1: return launch_interp_t<R, D, 1>(js, st);
-        case 2: return launch_interp_t<R, D, 2>(js, st);
-        case 3: return launch_interp_t<R, D, 3>(js, st);
-        case 4: return launch_interp_t<R, D, 4>(js, st);
-        case 5: return launch_interp_t<R, D, 5>(js, st);
-        case 6: return launch_interp_t<R, D, 6>(js, st);
-        case 7: return launch_interp_t<R, D, 7>(js, st);
-        default: return launch_interp_t<R, D, 8>(js, st);
-    }
-}
-
 template <class R, int D>
 static infft_status launch_forward(JobSet<R>& js, cudaStream_t st) {
     fill_prefixes(js, D, true);
@@ -1122,8 +568,10 @@ static infft_status launch_forward(JobSet<R>& js, cudaStream_t st) {
         INFFT_LAUNCHED();
     }
     if constexpr (D >= 2) {
-        int mi = 0;
-        if (interp_t_eligible<R, D>(js, &mi)) return launch_interp<R, D>(js, st, mi);
+        bool used = false;
+        if (D == 2) INFFT_TRY(interp2d_try<R>(js, st, &used));
+        else INFFT_TRY(interp3d_try<R>(js, st, &used));
+        if (used) return INFFT_OK;
     }
     size_t spw = 0;
     for (int j = 0; j < js.njobs; ++j) {

@@ -1,0 +1,218 @@
+// Two-dimensional spreading kernel (register rows) and its launcher.
+#include <algorithm>
+#include <type_traits>
+
+#include "spread.cuh"
+
+namespace infft {
+
+// ---------------------------------------------------------------------------------------
+// Two-dimensional spreading with the accumulators in registers.  One warp per work
+// item; lane l owns column l of the item's P x P padded tile (P = T + 2m + 1 <= 32).
+// The item's points are sorted by base row, so the rows a point can touch,
+// [oy, oy + 2m] (padded coordinates; one more row for B_opt slots), only move down:
+// each lane keeps those rows of its column in registers, adds the point's taps
+// (coefficient c_j psi_y[k] broadcast, times psi_x of its column), and when the next
+// point starts lower it stores the rows that no later point can reach.  Every padded
+// cell is stored exactly once, no shared-memory read-modify-write, no atomics.
+// Window values are computed once per point while staging 32 points per warp.
+template <class R, int MM, bool BOPT>
+__global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet<R> js) {
+    constexpr int W = 2 * MM + 1;              // window taps per axis
+    constexpr int WE = W + 1;                  // even stride of the staged rows (16-byte loads)
+    constexpr int WR = BOPT ? W + 1 : W;       // rows held in registers
+    constexpr bool F32 = sizeof(R) == 4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gitem = blockIdx.x * js.wpb + warp;
+    if (gitem >= js.pre_items[js.njobs]) return;
+    const int jb = find_job(js.pre_items, js.njobs, gitem);
+    const Job<R>& J = js.job[jb];
+    const int it = gitem - js.pre_items[jb];
+    const int4 item = J.items[it];
+    const int P = J.P, Ms = J.Ms, T = J.T;
+
+    unsigned char* base = smem_raw + (size_t)warp * js.smem_per_warp;
+    cx<R>* cy = reinterpret_cast<cx<R>*>(base);            // [32][WE] c_j psi_y (window mode)
+    R* psx = reinterpret_cast<R*>(cy + 32 * WE);            // [32][WE] psi_x
+    int* meta = reinterpret_cast<int*>(psx + 32 * WE);      // [32][3]  oy, ox, sorted index
+    cx<R>* cst = reinterpret_cast<cx<R>*>(meta + 96);       // [32]     c_j (B_opt mode)
+    float* poly = reinterpret_cast<float*>(cst + 32);       // [(WPOLY_DEG+1) * WP] window polynomial (16-byte rows)
+    const bool use_poly = F32 && !BOPT && J.wpoly != nullptr;
+    if (use_poly) {
+        for (int e = lane; e < (WPOLY_DEG + 1) * wpoly_stride(W); e += 32) poly[e] = J.wpoly[e];
+    }
+
+    const int ty = item.x / J.ntile, tx = item.x % J.ntile;
+    using V2 = typename std::conditional<F32, float2, double2>::type;
+    V2 acc[WR];  // (re, im) of the rows r0 .. r0 + WR - 1 of this lane's column
+#pragma unroll
+    for (int k = 0; k < WR; ++k) { acc[k].x = R(0); acc[k].y = R(0); }
+    int r0 = 0;  // padded row held in acc[0]
+    cx<R>* dst = J.padded + (size_t)it * P * P;
+    const bool col_ok = lane < P;
+    const int logMs = 31 - __clz(Ms);
+
+    for (int c0 = 0; c0 < item.z; c0 += 32) {
+        const int np = min(32, item.z - c0);
+        __syncwarp();
+        if (lane < np) {
+            const int i = item.y + c0 + lane;
+            const int j = __ldg(J.perm + i);
+            cx<R> fv = J.in[j];
+            if (J.mode == INFFT_MODE_DCF) fv = mul(J.w[i], fv);
+            const uint32_t cl = __ldg(J.cell + i);
+            const int cxl = (int)(cl & (uint32_t)(Ms - 1)), cyl = (int)(cl >> logMs);
+            meta[lane * 3 + 0] = cyl - ty * T;
+            meta[lane * 3 + 1] = cxl - tx * T;
+            meta[lane * 3 + 2] = i;
+            if (BOPT) {
+                cst[lane] = fv;
+            } else {
+                const R uy = J.u[(size_t)i * 2 + 0], ux = J.u[(size_t)i * 2 + 1];
+                R wy[W], wx[W];
+                bool done = false;
+                if constexpr (F32) {
+                    if (use_poly) {
+                        poly_taps2<W>(poly, uy, ux, wy, wx);
+                        done = true;
+                    }
+                }
+                if (!done) {
+#pragma unroll
+                    for (int s = 0; s < W; ++s) {
+                        wy[s] = tap_weight<R>(J.window, uy, s, MM, J.inv_m, J.beta);
+                        wx[s] = tap_weight<R>(J.window, ux, s, MM, J.inv_m, J.beta);
+                    }
+                }
+#pragma unroll
+                for (int s = 0; s < W; ++s) {
+                    cy[lane * WE + s] = scale(fv, wy[s]);
+                    psx[lane * WE + s] = wx[s];
+                }
+                cy[lane * WE + W] = mk<R>(0, 0);
+            }
+        }
+        __syncwarp();
+        for (int p = 0; p < np; ++p) {
+            const int oy = meta[p * 3 + 0], ox = meta[p * 3 + 1];
+            // store the rows above oy: no later point reaches them
+            while (r0 < oy) {
+                if (col_ok) dst[(size_t)r0 * P + lane] = mk<R>(acc[0].x, acc[0].y);
+#pragma unroll
+                for (int k = 0; k < WR - 1; ++k) acc[k] = acc[k + 1];
+                acc[WR - 1].x = R(0);
+                acc[WR - 1].y = R(0);
+                ++r0;
+            }
+            const int sx = lane - ox;
+            if (BOPT) {
+                constexpr int S = W + 1;
+                if (sx >= 0 && sx < S) {
+                    const int i = meta[p * 3 + 2];
+                    const cx<R> cv = cst[p];
+                    const cx<R>* cf = J.coef + (size_t)i * S * S + sx;
+#pragma unroll
+                    for (int k = 0; k < S; ++k) {
+                        const cx<R> b = cf[k * S];
+                        acc[k].x += b.re * cv.re + b.im * cv.im;   // conj(b) f
+                        acc[k].y += b.re * cv.im - b.im * cv.re;
+                    }
+                }
+            } else {
+                const bool in = (sx >= 0) && (sx < W);
+                const R wx = in ? psx[p * WE + (in ? sx : 0)] : R(0);
+                const cx<R>* cp = cy + p * WE;
+                if constexpr (F32) {
+                    // two complex coefficients per 16-byte broadcast load, one packed
+                    // two-wide FMA per row
+                    const float4* cp4 = reinterpret_cast<const float4*>(cp);
+                    const float2 ww = make_float2(wx, wx);
+#pragma unroll
+                    for (int k2 = 0; k2 < WE / 2; ++k2) {
+                        const float4 c = cp4[k2];
+                        acc[2 * k2] = __ffma2_rn(make_float2(c.x, c.y), ww, acc[2 * k2]);
+                        if (2 * k2 + 1 < W) acc[2 * k2 + 1] = __ffma2_rn(make_float2(c.z, c.w), ww, acc[2 * k2 + 1]);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < W; ++k) {
+                        const cx<R> c = cp[k];
+                        acc[k].x += c.re * wx;
+                        acc[k].y += c.im * wx;
+                    }
+                }
+            }
+        }
+    }
+    // remaining rows (including rows no point reached)
+    while (r0 < P) {
+        if (col_ok) dst[(size_t)r0 * P + lane] = mk<R>(acc[0].x, acc[0].y);
+#pragma unroll
+        for (int k = 0; k < WR - 1; ++k) acc[k] = acc[k + 1];
+        acc[WR - 1].x = R(0);
+        acc[WR - 1].y = R(0);
+        ++r0;
+    }
+}
+
+// register-row spreading for d = 2 when every job has the same m (2..7) and P <= 32
+template <class R, int MM, bool BOPT>
+static infft_status launch_spread2d_m(JobSet<R>& js, cudaStream_t st) {
+    constexpr int W = 2 * MM + 1;
+    constexpr int WE = W + 1;
+    size_t spw = 32 * WE * sizeof(cx<R>) + 32 * WE * sizeof(R) + 96 * sizeof(int) + 32 * sizeof(cx<R>) +
+                 (WPOLY_DEG + 1) * wpoly_stride(W) * sizeof(float);
+    spw = (spw + 15) & ~(size_t)15;
+    js.smem_per_warp = (int)spw;
+    js.wpb = 4;
+    const int nitems = js.pre_items[js.njobs];
+    if (nitems == 0) return INFFT_OK;
+    const size_t smem = spw * js.wpb;
+    INFFT_CUDA(cudaFuncSetAttribute(k_spread2d<R, MM, BOPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_spread2d<R, MM, BOPT><<<(nitems + js.wpb - 1) / js.wpb, 32 * js.wpb, smem, st>>>(js);
+    INFFT_LAUNCHED();
+    return INFFT_OK;
+}
+
+template <class R, bool BOPT>
+static infft_status launch_spread2d(JobSet<R>& js, cudaStream_t st, int m) {
+    switch (m) {
+        case 2: return launch_spread2d_m<R, 2, BOPT>(js, st);
+        case 3: return launch_spread2d_m<R, 3, BOPT>(js, st);
+        case 4: return launch_spread2d_m<R, 4, BOPT>(js, st);
+        case 5: return launch_spread2d_m<R, 5, BOPT>(js, st);
+        case 6: return launch_spread2d_m<R, 6, BOPT>(js, st);
+        default: return launch_spread2d_m<R, 7, BOPT>(js, st);
+    }
+}
+
+template <class R>
+static bool spread2d_eligible(const JobSet<R>& js, int* m_out, bool* bopt_out) {
+    if (js.njobs < 1) return false;
+    const int m = js.job[0].m;
+    const bool bopt = js.job[0].mode == INFFT_MODE_BOPT;
+    for (int j = 0; j < js.njobs; ++j) {
+        const Job<R>& J = js.job[j];
+        if (J.d != 2 || J.m != m || (J.mode == INFFT_MODE_BOPT) != bopt || J.P > 32) return false;
+    }
+    if (m < 2 || m > 7) return false;
+    *m_out = m;
+    *bopt_out = bopt;
+    return true;
+}
+
+template <class R>
+infft_status spread2d_try(JobSet<R>& js, cudaStream_t st, bool* used) {
+    int m = 0;
+    bool bopt = false;
+    *used = false;
+    if (!spread2d_eligible(js, &m, &bopt)) return INFFT_OK;
+    *used = true;
+    return bopt ? launch_spread2d<R, true>(js, st, m) : launch_spread2d<R, false>(js, st, m);
+}
+
+template infft_status spread2d_try<float>(JobSet<float>&, cudaStream_t, bool*);
+template infft_status spread2d_try<double>(JobSet<double>&, cudaStream_t, bool*);
+
+}  // namespace infft
