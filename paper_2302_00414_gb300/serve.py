@@ -3,7 +3,8 @@
 Requests name a point set and carry a sample vector f.  The loop keeps plans (sorted
 points, weights, tables) on the device across requests; a request for an unknown point
 set is parked while a worker thread builds its plan and weights (Algorithm 3.6) on a
-stream of its own.  Every iteration of ``step()``:
+low-priority stream of its own; reconstructions run on high-priority streams, so that the
+device schedules their blocks ahead of the precompute's.  Every iteration of ``step()``:
 
 * retires batches whose completion event has fired and stamps their latencies;
 * admits ready requests into a new batch as soon as one of the ``streams`` slots is free
@@ -83,8 +84,10 @@ class Backend:
     def free_bytes(self) -> int:
         return int(self.torch.cuda.mem_get_info()[0])
 
-    def new_stream(self):
-        return self.torch.cuda.Stream()
+    def new_stream(self, priority: int = 0):
+        # lower number = higher priority: the device scheduler then prefers blocks of the
+        # reconstruction streams over those of the precompute stream
+        return self.torch.cuda.Stream(priority=priority)
 
     def launch(self, plans, fs, stream, slots):
         torch = self.torch
@@ -113,7 +116,7 @@ class Server:
         self.max_repeat = max_repeat
         self.mem_budget = mem_budget
         self.clock = clock
-        self.streams = [backend.new_stream() for _ in range(streams)]
+        self.streams = [backend.new_stream(priority=-1) for _ in range(streams)]
         self.free_streams = list(range(streams))
         self.plans: Dict[Any, Any] = {}
         self.plan_meta: Dict[Any, PointSet] = {}
@@ -123,18 +126,20 @@ class Server:
         self.plan_refs: Dict[Any, int] = collections.Counter()   # requests queued or in flight
         self.resident_bytes = 0        # plans on the device
         self.reserved: Dict[Any, int] = {}   # estimates of plans being built
+        self._reserved_total = 0
         self.pending: collections.deque = collections.deque()
         self.parked: Dict[Any, List[Request]] = collections.defaultdict(list)
+        self._n_parked = 0
         self.inflight: List[tuple] = []
         self.completed: List[Request] = []
         self.stats = collections.Counter()
-        self._retry: List[PointSet] = []
+        self._retry: collections.deque = collections.deque()   # sets waiting for memory, FIFO
         self._deferred_keys: set = set()
         self.build_times: List[tuple] = []    # (key, seconds) of every plan built
         self._lock = threading.Lock()
         self._work: queue.Queue = queue.Queue()
         self._ready: queue.Queue = queue.Queue()
-        self._pstream = backend.new_stream()
+        self._pstream = backend.new_stream(priority=0)
         self._worker = threading.Thread(target=self._precompute_loop, daemon=True)
         self._worker.start()
 
@@ -160,10 +165,10 @@ class Server:
     def _make_room(self, need: int) -> bool:
         """Evict LRU plans that are not in flight until `need` more bytes fit."""
         def fits():
-            held = self.resident_bytes + sum(self.reserved.values())
+            held = self.resident_bytes + self._reserved_total
             if self.mem_budget is not None and held + need > self.mem_budget:
                 return False
-            return self.be.free_bytes() - sum(self.reserved.values()) > need
+            return self.be.free_bytes() - self._reserved_total > need
         while not fits():
             idle = [k for k in self.plans if self.plan_refs[k] == 0 and k not in self.pinned]
             if not idle:
@@ -183,19 +188,27 @@ class Server:
             return
         first = req.key not in self.parked or not self.parked[req.key]
         self.parked[req.key].append(req)
+        self._n_parked += 1
         if first:
             ps = self.plan_meta[req.key]
             self.stats["new_sets"] += 1
             self._deferred_admit(ps)
 
-    def _deferred_admit(self, ps: PointSet):
+    def _admit(self, ps: PointSet) -> bool:
+        """Reserve memory for a new point set and queue its build; False if it does not fit."""
         need = self.be.estimate_bytes(ps)
         if self._make_room(need):
             self.reserved[ps.key] = need
+            self._reserved_total += need
             self._work.put(ps)
-        elif not self.plans and not self.reserved:
+            return True
+        if not self.plans and not self.reserved:
             raise MemoryError(f"point set {ps.key!r} needs ~{need} bytes, more than the budget")
-        else:
+        return False
+
+    def _deferred_admit(self, ps: PointSet):
+        # sets wait in arrival order: a new set does not overtake one already waiting
+        if self._retry or not self._admit(ps):
             if ps.key not in self._deferred_keys:
                 self._deferred_keys.add(ps.key)
                 self.stats["admit_deferred"] += 1
@@ -227,18 +240,17 @@ class Server:
                 break
             if err is not None:
                 raise err
-            self.reserved.pop(key, None)
+            self._reserved_total -= self.reserved.pop(key, 0)
             self.plans[key] = plan
             self.plan_used[key] = now()
             self.plan_size[key] = self.be.plan_bytes(plan)
             self.resident_bytes += self.plan_size[key]
             waiting = self.parked.pop(key, [])
+            self._n_parked -= len(waiting)
             self.plan_refs[key] += len(waiting)
             self.pending.extend(waiting)
-        if self._retry:
-            retry, self._retry = self._retry, []
-            for ps in retry:
-                self._deferred_admit(ps)
+        while self._retry and self._admit(self._retry[0]):
+            self._retry.popleft()
         # launch: one batch per (d, precision) group into free stream slots.  The j-th
         # request for a point set in the batch on stream s uses the plan's scratch set
         # s * max_repeat + j, so batches on different streams never share scratch.
@@ -283,7 +295,7 @@ class Server:
                 self.inflight.append((ev, reqs, sidx, outs))
                 self.stats["batches"] += 1
                 self.stats["max_inflight"] = max(self.stats["max_inflight"], len(self.inflight))
-        return len(self.pending) + sum(len(v) for v in self.parked.values()) + \
+        return len(self.pending) + self._n_parked + \
             sum(len(r) for _, r, _, _ in self.inflight)
 
     def drain(self, timeout: float = 600.0):

@@ -36,8 +36,8 @@ class FakeBackend:
     def free_bytes(self):
         return self.free
 
-    def new_stream(self):
-        return object()
+    def new_stream(self, priority=0):
+        return ("stream", priority)
 
     def launch(self, plans, fs, stream, slots):
         self.launches.append([p.key for p in plans])
@@ -179,4 +179,10 @@ def test_pinned_point_sets_are_never_evicted():
     assert len(s.completed) == 12
     assert 0 not in be.released and 0 in s.plans
     assert s.stats["evicted"] > 0
+    s.close()
+
+
+def test_reconstruction_streams_outrank_the_precompute_stream():
+    s = Server(FakeBackend(), streams=3)
+    assert all(st[1] < s._pstream[1] for st in s.streams)
     s.close()
