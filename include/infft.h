@@ -81,6 +81,13 @@ enum {
 };
 
 /* options of infft_optimize_B */
+/* options of infft_weights_opts */
+enum {
+    INFFT_WEIGHTS_AUTO = 0,       /* Toeplitz products where they apply, else NFFT products  */
+    INFFT_WEIGHTS_NFFT = 1,       /* an NFFT and an adjoint NFFT per iteration (as printed)  */
+    INFFT_WEIGHTS_TOEPLITZ = 2    /* convolution form of A^*A (second kind only)             */
+};
+
 enum {
     INFFT_BOPT_PATTERN_2M2 = 0,   /* 2m+2 consecutive indices per coordinate (default)       */
     INFFT_BOPT_PATTERN_PAPER = 1, /* the index set I_{Msigma,m}(x_j) of eq. indexset_x         */
@@ -114,7 +121,8 @@ infft_status infft_plan(int d, int M, int64_t N, const double* x, double sigma, 
  * w = conj(A_2M u).  Otherwise: CG on A_2M A_2M^* q = 1_N (first kind,
  * eq. normal_equations_first_kind_double), w = conj(q).  Matrix products are
  * float64 NFFTs (Algorithms 2.1 / 2.4) at degree 2M with oversampling 2 and
- * truncation m_cg (<= 0 selects 8 for d <= 2 and 4 for d = 3); CG vectors,
+ * truncation m_cg (<= 0 selects 8 for d <= 2 and 4 for d = 3), or, in the second
+ * kind, the convolution form of infft_weights_opts below; CG vectors,
  * inner products and updates are float64.  x0 = 0, stop when
  * ||r||_2 / ||b||_2 <= rel_tol or after max_iter iterations.
  *   residual_inf : (out, may be NULL) max_k |[A_2M^T w]_k - delta_{0,k}| over
@@ -125,6 +133,24 @@ infft_status infft_plan(int d, int M, int64_t N, const double* x, double sigma, 
  */
 infft_status infft_weights(infft_plan_t plan, int max_iter, double rel_tol, int m_cg,
                            double* residual_inf, int* iters, void* stream);
+
+/*
+ * infft_weights_opts -- infft_weights with a choice of how the CG applies its matrix.
+ *   INFFT_WEIGHTS_NFFT: every iteration applies A_2M^* A_2M (or A_2M A_2M^*) by a
+ *     float64 NFFT and an adjoint NFFT, as Algorithm 3.6 prints it.
+ *   INFFT_WEIGHTS_TOEPLITZ: second kind only ((2M)^d <= N) and 4M <= 4096.  The entries
+ *     of A_2M^* A_2M depend on k - k' only, [A^*A]_{k,k'} = t(k - k') with
+ *     t(n) = sum_j exp(-2 pi i n x_j) on I_4M.  t is computed once from 2^d adjoint
+ *     NFFTs at degree 2M of the samples exp(-2 pi i s x_j), s in {-M, M}^d; each
+ *     iteration is then a circular convolution of period 4M: two float64 FFTs of
+ *     (4M)^d points and a pointwise product.  Temporary device memory of about
+ *     4 (4M)^d complex128 values.
+ *   INFFT_WEIGHTS_AUTO (0, what infft_weights uses): TOEPLITZ where it applies, else NFFT.
+ * Other arguments, results and errors as infft_weights; INFFT_EUNSUPPORTED when
+ * TOEPLITZ is asked for where it does not apply, INFFT_EINVAL for unknown options.
+ */
+infft_status infft_weights_opts(infft_plan_t plan, int max_iter, double rel_tol, int m_cg, unsigned opts,
+                                double* residual_inf, int* iters, void* stream);
 
 /* infft_set_weights / infft_get_weights -- N complex128 weights in the caller's
  * point order (host or device).  set marks the plan ready for INFFT_MODE_DCF. */

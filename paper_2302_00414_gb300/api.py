@@ -22,6 +22,7 @@ FP32, FP64 = 1, 2
 WIN_KB, WIN_BSPLINE, WIN_DIRICHLET = 0, 4, 8
 MODE_PLAIN, MODE_DCF, MODE_BOPT = 0, 1, 2
 BOPT_PATTERN_2M2, BOPT_PATTERN_PAPER, BOPT_REAL = 0, 1, 2
+WEIGHTS_AUTO, WEIGHTS_NFFT, WEIGHTS_TOEPLITZ = 0, 1, 2
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOTCONV", "ETIMEOUT", "ESTATE", "EUNSUPPORTED"]
 
 
@@ -38,6 +39,8 @@ _SIGS = {
                              C.POINTER(C.c_void_p)]),
     "infft_weights": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
                                 C.POINTER(C.c_int), C.c_void_p]),
+    "infft_weights_opts": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_uint, C.POINTER(C.c_double),
+                                     C.POINTER(C.c_int), C.c_void_p]),
     "infft_set_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "infft_get_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "infft_optimize_B": (C.c_int, [C.c_void_p, C.c_uint, C.POINTER(C.c_double), C.c_void_p]),
@@ -107,10 +110,13 @@ def infft_plan(d, M, N, x_ptr, sigma, m, flags, stream=0):
     return load().infft_plan(d, M, N, x_ptr, sigma, m, flags, stream, C.byref(out)), out.value
 
 
-def infft_weights(plan, max_iter, rel_tol, m_cg=0, stream=0):
+def infft_weights(plan, max_iter, rel_tol, m_cg=0, stream=0, opts=0):
     res = C.c_double(float("nan"))
     it = C.c_int(0)
-    s = load().infft_weights(plan, max_iter, rel_tol, m_cg, C.byref(res), C.byref(it), stream)
+    if opts:
+        s = load().infft_weights_opts(plan, max_iter, rel_tol, m_cg, opts, C.byref(res), C.byref(it), stream)
+    else:
+        s = load().infft_weights(plan, max_iter, rel_tol, m_cg, C.byref(res), C.byref(it), stream)
     return s, res.value, it.value
 
 
@@ -225,8 +231,12 @@ class Plan:
         except Exception:
             pass
 
-    def weights(self, max_iter: int = 1000, rel_tol: float = 1e-13, m_cg: int = 0, stream=None, check=True):
-        s, res, it = infft_weights(self.handle, max_iter, rel_tol, m_cg, _stream(stream))
+    def weights(self, max_iter: int = 1000, rel_tol: float = 1e-13, m_cg: int = 0, stream=None, check=True,
+                method: str = "auto"):
+        """Algorithm 3.6; method "nfft" (products by NFFTs), "toeplitz" (convolution form,
+        second kind only) or "auto"."""
+        opts = {"auto": WEIGHTS_AUTO, "nfft": WEIGHTS_NFFT, "toeplitz": WEIGHTS_TOEPLITZ}[method]
+        s, res, it = infft_weights(self.handle, max_iter, rel_tol, m_cg, _stream(stream), opts)
         if check and s not in (OK, ENOTCONV):
             _check(s)
         return {"status": s, "residual_inf": res, "iters": it}

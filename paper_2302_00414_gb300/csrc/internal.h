@@ -123,4 +123,11 @@ infft_status run_jobs(const std::vector<Job<R>>& jobs, cudaStream_t st, bool for
 template <class R>
 infft_status run_jobs(const Job<R>* jobs, size_t count, cudaStream_t st, bool forward, cudaEvent_t* ev = nullptr);
 
+// The d FFT passes of one job alone (no spreading, merge or interpolation): forward = true
+// maps J.in (M^d over I_M, times J.dinv per axis) to J.grid (Ms^d) with sign +; forward =
+// false maps J.grid to J.out (M^d, times J.dinv per axis) with sign -.  Uses J.tw, J.tmp1,
+// J.tmp2 (each large enough for the intermediate tensors) and J.d, J.M, J.Ms.
+template <class R>
+infft_status run_fft_passes(const Job<R>& J, cudaStream_t st, bool forward);
+
 }  // namespace infft

@@ -622,6 +622,41 @@ infft_status run_jobs(const Job<R>* jobs, size_t count, cudaStream_t st, bool fo
     return INFFT_OK;
 }
 
+template <class R, int D>
+static infft_status fft_passes_d(JobSet<R>& js, cudaStream_t st, bool forward) {
+    fill_prefixes(js, D, forward);
+    const int n = js.job[0].Ms;
+    const size_t fsmem = (size_t)js.L * (n + n / 16) * sizeof(cx<R>);
+    if (forward) {
+        INFFT_CUDA(cudaFuncSetAttribute(k_fft<R, D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
+        for (int p = 0; p < D; ++p) {
+            k_fft<R, D, true><<<js.pre_fft[p][1], 256, fsmem, st>>>(js, p);
+            INFFT_LAUNCHED();
+        }
+    } else {
+        INFFT_CUDA(cudaFuncSetAttribute(k_fft<R, D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
+        for (int p = 0; p < D; ++p) {
+            k_fft<R, D, false><<<js.pre_fft[p][1], 256, fsmem, st>>>(js, p);
+            INFFT_LAUNCHED();
+        }
+    }
+    return INFFT_OK;
+}
+
+template <class R>
+infft_status run_fft_passes(const Job<R>& J, cudaStream_t st, bool forward) {
+    JobSet<R> js;
+    memset(&js, 0, sizeof(js));
+    js.njobs = 1;
+    js.job[0] = J;
+    switch (J.d) {
+        case 1: return fft_passes_d<R, 1>(js, st, forward);
+        case 2: return fft_passes_d<R, 2>(js, st, forward);
+        default: return fft_passes_d<R, 3>(js, st, forward);
+    }
+}
+
+template infft_status run_fft_passes<double>(const Job<double>&, cudaStream_t, bool);
 template infft_status run_jobs<float>(const std::vector<Job<float>>&, cudaStream_t, bool, cudaEvent_t*);
 template infft_status run_jobs<double>(const std::vector<Job<double>>&, cudaStream_t, bool, cudaEvent_t*);
 template infft_status run_jobs<float>(const Job<float>*, size_t, cudaStream_t, bool, cudaEvent_t*);

@@ -13,6 +13,8 @@
 // are already in the order the spreading kernels read them.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <functional>
 #include <vector>
 
 #include "internal.h"
@@ -151,6 +153,138 @@ __global__ void k_sort_weights(const cx<double>* __restrict__ master, const int*
     sorted[i] = mk<R>((R)v.re, (R)v.im);
 }
 
+// ---------------------------------------------------------------------------------------
+// Toeplitz form of the second-kind products.  For A = A_2M (N x |I_2M|),
+//   [A^* A]_{k,k'} = sum_j exp(-2 pi i (k - k') x_j) = t(k - k'),  k - k' in (-2M, 2M)^d,
+// so A^* A u is a d-variate discrete convolution of t with u.  t on I_4M is obtained once
+// from 2^d adjoint NFFTs at degree 2M of modulated unit samples,
+//   t(s + k) = sum_j exp(-2 pi i s x_j) exp(-2 pi i k x_j),  s in {-M, M}^d, k in I_2M,
+// and the convolution is a circular one of period L = 4M (u zero-padded):
+//   A^* A u = crop_{I_2M} F_L^- ( c_hat .* F_L^+ u ),  c_hat = L^{-d} F_L^+ t,
+// where F_L^+ / F_L^- are the unnormalised DFTs with sign + / - (the pruned FFT passes with
+// unit deconvolution factors).  Each CG iteration is then two FFTs of L^d points instead of
+// an NFFT and an adjoint NFFT.
+
+// f_j = exp(-2 pi i sum_t s_t x_{j,t}), s_t = -M2/2 or +M2/2 by bit t of `bits`; each
+// s_t x_t is exact (M2/2 is a power of two) and is reduced mod 1 before the sum
+__global__ void k_modulate(const double* __restrict__ x, int N, int d, int M2, int bits, cx<double>* __restrict__ f) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    double ph = 0.0;
+    for (int t = 0; t < d; ++t) {
+        const double st = ((bits >> t) & 1) ? 0.5 * M2 : -0.5 * M2;
+        const double v = st * x[(size_t)j * d + t];
+        ph += v - rint(v);
+    }
+    double sn, cs;
+    sincospi(-2.0 * ph, &sn, &cs);
+    f[j] = mk<double>(cs, sn);
+}
+
+// place the degree-2M result of shift `bits` into I_4M: entry (i_t)_t of h goes to
+// (i_t + M2 bit_t)_t of t (C order, 2 M2 per axis)
+__global__ void k_scatter_t(const cx<double>* __restrict__ h, int d, int M2, int bits, cx<double>* __restrict__ t) {
+    long long K = 1;
+    for (int q = 0; q < d; ++q) K *= M2;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K) return;
+    long long rem = i, dst = 0, stride = 1;
+    for (int q = d - 1; q >= 0; --q) {
+        const int it = (int)(rem % M2);
+        rem /= M2;
+        dst += (long long)(it + (((bits >> q) & 1) ? M2 : 0)) * stride;
+        stride *= 2LL * M2;
+    }
+    t[dst] = h[i];
+}
+
+__global__ void k_cmul(cx<double>* __restrict__ a, const cx<double>* __restrict__ b, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        a[i] = mul(a[i], b[i]);
+}
+
+__global__ void k_fill_real(double* __restrict__ a, int n, double v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = v;
+}
+
+__global__ void k_twiddles(int L, cx<double>* __restrict__ tw) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < L / 2) {
+        double sn, cs;
+        sincospi(2.0 * i / L, &sn, &cs);
+        tw[i] = mk<double>(cs, -sn);
+    }
+}
+
+struct ToeplitzOp {
+    Job<double> fwd;     // u (I_2M) -> G (L^d), sign +
+    Job<double> adj;     // G -> A^*A u (I_2M), sign -
+    cx<double>* G = nullptr;
+    const cx<double>* chat = nullptr;
+    long long Ld = 0;
+};
+
+static infft_status nfft64(infft_plan_s* q, bool forward, const void* in, void* out, cudaStream_t st);
+
+// Build the operator: t by 2^d modulated adjoint NFFTs of the degree-2M sub-plan, then c_hat.
+static infft_status toeplitz_setup(const infft_plan_s* p, infft_plan_s* sub, int M2, cudaStream_t st,
+                                   const std::function<void*(size_t)>& alloc, ToeplitzOp& op) {
+    const int d = p->d, N = (int)p->N, L = 2 * M2;
+    long long Ld = 1, K = 1;
+    for (int t = 0; t < d; ++t) { Ld *= L; K *= M2; }
+    cx<double>* G = (cx<double>*)alloc(Ld * 16);
+    cx<double>* chat = (cx<double>*)alloc(Ld * 16);
+    cx<double>* t1 = d >= 2 ? (cx<double>*)alloc(Ld * 16) : nullptr;
+    cx<double>* t2 = d == 3 ? (cx<double>*)alloc(Ld * 16) : nullptr;
+    cx<double>* fm = (cx<double>*)alloc((size_t)N * 16);
+    cx<double>* hb = (cx<double>*)alloc(K * 16);
+    cx<double>* tw = (cx<double>*)alloc((size_t)(L / 2) * 16);
+    double* ones = (double*)alloc((size_t)M2 * 8);
+    double* invL = (double*)alloc((size_t)L * 8);
+    if (!G || !chat || (d >= 2 && !t1) || (d == 3 && !t2) || !fm || !hb || !tw || !ones || !invL) {
+        set_error("Toeplitz buffers: out of device memory");
+        return INFFT_ENOMEM;
+    }
+    k_twiddles<<<(L / 2 + 255) / 256, 256, 0, st>>>(L, tw);
+    INFFT_LAUNCHED();
+    k_fill_real<<<(M2 + 255) / 256, 256, 0, st>>>(ones, M2, 1.0);
+    INFFT_LAUNCHED();
+    k_fill_real<<<(L + 255) / 256, 256, 0, st>>>(invL, L, 1.0 / L);
+    INFFT_LAUNCHED();
+    // t on I_4M, stored in G
+    for (int bits = 0; bits < (1 << d); ++bits) {
+        k_modulate<<<(N + 255) / 256, 256, 0, st>>>(p->x64, N, d, M2, bits, fm);
+        INFFT_LAUNCHED();
+        INFFT_TRY(nfft64(sub, false, fm, hb, st));
+        k_scatter_t<<<(unsigned)((K + 255) / 256), 256, 0, st>>>(hb, d, M2, bits, G);
+        INFFT_LAUNCHED();
+    }
+    Job<double> J;
+    memset(&J, 0, sizeof(J));
+    J.d = d; J.tw = tw; J.tmp1 = t1; J.tmp2 = t2;
+    // c_hat = L^{-d} F_L^+ t: every frequency of I_4M is an input (M = Ms = L)
+    J.M = L; J.Ms = L; J.dinv = invL; J.in = G; J.grid = chat;
+    INFFT_TRY(run_fft_passes<double>(J, st, true));
+    op.fwd = J;
+    op.fwd.M = M2; op.fwd.dinv = ones; op.fwd.grid = G;
+    op.adj = op.fwd;
+    op.G = G;
+    op.chat = chat;
+    op.Ld = Ld;
+    return INFFT_OK;
+}
+
+// q = A^* A p through the Toeplitz operator
+static infft_status toeplitz_apply(ToeplitzOp& op, const cx<double>* pin, cx<double>* qout, cudaStream_t st) {
+    op.fwd.in = pin;
+    INFFT_TRY(run_fft_passes<double>(op.fwd, st, true));
+    k_cmul<<<1024, 256, 0, st>>>(op.G, op.chat, op.Ld);
+    INFFT_LAUNCHED();
+    op.adj.out = qout;
+    return run_fft_passes<double>(op.adj, st, false);
+}
+
 static infft_status nfft64(infft_plan_s* q, bool forward, const void* in, void* out, cudaStream_t st) {
     std::vector<Job<double>> jobs{make_job<double>(q, INFFT_MODE_PLAIN, in, out)};
     return run_jobs<double>(jobs, st, forward);
@@ -172,8 +306,9 @@ static infft_status ensure_weight_buffers(infft_plan_s* p) {
     return INFFT_OK;
 }
 
-static infft_status weights_impl(infft_plan_s* p, int max_iter, double rel_tol, int m_cg, double* residual_inf,
-                                 int* iters_out, cudaStream_t st, std::vector<void*>& tmp, infft_plan_t& sub) {
+static infft_status weights_impl(infft_plan_s* p, int max_iter, double rel_tol, int m_cg, unsigned opts,
+                                 double* residual_inf, int* iters_out, cudaStream_t st, std::vector<void*>& tmp,
+                                 infft_plan_t& sub) {
     const int d = p->d, M2 = 2 * p->M;
     const int N = (int)p->N;
     if (m_cg <= 0) m_cg = (d <= 2) ? 8 : 4;
@@ -183,6 +318,13 @@ static infft_status weights_impl(infft_plan_s* p, int max_iter, double rel_tol, 
     long long K = 1;
     for (int t = 0; t < d; ++t) K *= M2;
     const bool second_kind = K <= N;
+    // Toeplitz products need the second kind and FFT lines of 4M <= 4096 points
+    const bool toeplitz_ok = second_kind && 2 * M2 <= 4096;
+    if ((opts & INFFT_WEIGHTS_TOEPLITZ) && !toeplitz_ok) {
+        set_error("Toeplitz CG needs (2M)^d <= N and 4M <= 4096");
+        return INFFT_EUNSUPPORTED;
+    }
+    const bool toeplitz = toeplitz_ok && !(opts & INFFT_WEIGHTS_NFFT);
     const long long n = second_kind ? K : N;   // CG unknowns
     const long long aux_n = second_kind ? N : K;
     auto alloc = [&](size_t bytes) -> void* {
@@ -206,6 +348,8 @@ static infft_status weights_impl(infft_plan_s* p, int max_iter, double rel_tol, 
         return INFFT_ENOMEM;
     }
     const int eb = 1024, et = 256;
+    ToeplitzOp top;
+    if (toeplitz) INFFT_TRY(toeplitz_setup(p, sub, M2, st, [&](size_t b) { return alloc(b); }, top));
     // x = 0; r = b; p = b
     INFFT_CUDA(cudaMemsetAsync(x, 0, n * 16, st));
     if (second_kind) {
@@ -230,7 +374,9 @@ static infft_status weights_impl(infft_plan_s* p, int max_iter, double rel_tol, 
     bool conv = false;
     for (it = 0; it < max_iter; ++it) {
         // q = op(p)
-        if (second_kind) {
+        if (toeplitz) {
+            INFFT_TRY(toeplitz_apply(top, pv, qv, st));   // A^* A p as a convolution
+        } else if (second_kind) {
             INFFT_TRY(nfft64(sub, true, pv, aux, st));    // A p   (K -> N)
             INFFT_TRY(nfft64(sub, false, aux, qv, st));   // A^* (A p)
         } else {
@@ -298,16 +444,26 @@ using namespace infft;
 
 extern "C" {
 
-infft_status infft_weights(infft_plan_t p, int max_iter, double rel_tol, int m_cg, double* residual_inf, int* iters,
-                           void* stream) {
+infft_status infft_weights_opts(infft_plan_t p, int max_iter, double rel_tol, int m_cg, unsigned opts,
+                                double* residual_inf, int* iters, void* stream) {
     if (!p || max_iter < 1 || !(rel_tol >= 0)) { set_error("invalid weights arguments"); return INFFT_EINVAL; }
+    if ((opts & ~(unsigned)(INFFT_WEIGHTS_NFFT | INFFT_WEIGHTS_TOEPLITZ)) ||
+        ((opts & INFFT_WEIGHTS_NFFT) && (opts & INFFT_WEIGHTS_TOEPLITZ))) {
+        set_error("invalid weights options %u", opts);
+        return INFFT_EINVAL;
+    }
     std::vector<void*> tmp;
     infft_plan_t sub = nullptr;
-    infft_status s = weights_impl(p, max_iter, rel_tol, m_cg, residual_inf, iters, (cudaStream_t)stream, tmp, sub);
+    infft_status s = weights_impl(p, max_iter, rel_tol, m_cg, opts, residual_inf, iters, (cudaStream_t)stream, tmp, sub);
     cudaStreamSynchronize((cudaStream_t)stream);
     for (void* q : tmp) cudaFree(q);
     if (sub) infft_destroy(sub);
     return s;
+}
+
+infft_status infft_weights(infft_plan_t p, int max_iter, double rel_tol, int m_cg, double* residual_inf, int* iters,
+                           void* stream) {
+    return infft_weights_opts(p, max_iter, rel_tol, m_cg, 0u, residual_inf, iters, stream);
 }
 
 infft_status infft_set_weights(infft_plan_t p, const void* w, void* stream) {

@@ -44,24 +44,59 @@ def test_equispaced_weights_one_over_N():
     assert np.max(np.abs(w - 1.0 / x.shape[0])) < 1e-12
 
 
-@pytest.mark.parametrize("d,M,N", [(2, 8, 600), (2, 16, 1500)])
-def test_second_kind_weights_match_dense_solution(d, M, N):
+# (d, M, N, m_cg, weight tolerance, residual tolerance): the CG's matrix is exact only to
+# the float64 NFFT accuracy of m_cg (about 4e-14 relative at m_cg = 8, 2e-8 at 5, the largest
+# a float64 three-dimensional padded tile fits in shared memory); ill-conditioned random sets
+# amplify it in the residual
+SECOND_KIND = [(2, 8, 600, 8, 1e-8, 1e-9), (2, 16, 1500, 8, 1e-8, 1e-9), (1, 32, 100, 8, 1e-8, 1e-9),
+               (3, 4, 700, 5, 1e-5, 1e-6)]
+
+
+@pytest.mark.parametrize("method", ["nfft", "toeplitz"])
+@pytest.mark.parametrize("d,M,N,m_cg,wtol,etol", SECOND_KIND)
+def test_second_kind_weights_match_dense_solution(d, M, N, m_cg, wtol, etol, method):
     L, torch = lib_or_skip()
     x = inputs.random_points(N, d, 21)
-    p = L.Plan(x, M, 2.0, 6, "fp64")
-    info = p.weights(max_iter=2000, rel_tol=1e-13)
+    p = L.Plan(x, M, 2.0, min(6, M - 1), "fp64")
+    info = p.weights(max_iter=2000, rel_tol=1e-13, m_cg=m_cg, method=method)
     w = p.get_weights()
     w_ref = WT.weights(x, M)
-    assert rel(w, w_ref) < 1e-8
+    assert rel(w, w_ref) < wtol
     eps = WT.residual_inf(x, w, M)
-    assert eps < 1e-10 and info["residual_inf"] == pytest.approx(eps, rel=0.5, abs=1e-12)
+    assert eps < etol and info["residual_inf"] == pytest.approx(eps, rel=0.5, abs=etol / 100)
     fh = inputs.coeffs_complex((M,) * d, 22)
     f = FO.ndft(x, fh, M)
     # Theorem 3.14(i) on the exact sums with the GPU weights ...
     assert rel(WT.reconstruct_exact(x, f, w, M), fh) <= M ** d * eps + 1e-13
-    # ... and the GPU reconstruction adds at most the NFFT approximation error
+    # ... and the GPU reconstruction adds at most the NFFT approximation error, which scales
+    # with sum_j |w_j f_j| (each coefficient's error is at most the window error times it)
     h = p.adjoint(to_dev(torch, f), mode=L.MODE_DCF).cpu().numpy()
-    assert rel(h, fh) <= M ** d * eps + kb_bound(6, 2.0)
+    h_exact = WT.reconstruct_exact(x, f, w, M)
+    scale = np.sqrt(M ** d) * np.sum(np.abs(w * f))
+    assert np.linalg.norm(h.ravel() - h_exact.ravel()) <= kb_bound(min(6, M - 1), 2.0) * scale
+
+
+@pytest.mark.parametrize("d,M,N,m_cg,wtol,etol", [(2, 32, 6000, 8, 1e-7, 1e-9), (3, 8, 5000, 5, 1e-5, 1e-6)])
+def test_toeplitz_and_nfft_products_reach_the_same_weights(d, M, N, m_cg, wtol, etol):
+    """Both forms of the CG apply the same matrix A_2M^* A_2M up to NFFT accuracy."""
+    L, torch = lib_or_skip()
+    x = inputs.random_points(N, d, 23)
+    ws, res = [], []
+    for method in ("nfft", "toeplitz"):
+        p = L.Plan(x, M, 2.0, 4, "fp64")
+        info = p.weights(max_iter=3000, rel_tol=1e-13, m_cg=m_cg, method=method)
+        ws.append(p.get_weights())
+        res.append(info["residual_inf"])
+    assert rel(ws[1], ws[0]) < wtol
+    assert max(res) < etol
+
+
+def test_toeplitz_needs_the_second_kind():
+    L, torch = lib_or_skip()
+    x = inputs.random_points(50, 1, 31)
+    p = L.Plan(x, 64, 2.0, 6, "fp64")     # |I_2M| = 128 > N: first kind
+    with pytest.raises(L.InfftError):
+        p.weights(max_iter=10, method="toeplitz")
 
 
 def test_first_kind_weights_least_squares():
