@@ -1,5 +1,6 @@
 """Optimisation of the sparse matrix B (Section 4, Algorithm 4.3) and the
-reconstruction of Algorithm 4.4, from the definitions.
+reconstruction of Algorithm 4.4, from the definitions, and the inverse adjoint NFFT of
+Remark 4.6 with the same B_opt.
 
 For every column l in I_{M_sigma} the nonzeros b_l of B_opt solve the least
 squares problem (eq. opt_overdet_columnwise)
@@ -32,8 +33,8 @@ import numpy as np
 
 from . import windows as W
 from .fourier import index_set
-from .nfft import (PATTERN_2M2, PATTERN_PAPER, grid_to_coeffs, point_slots, reduce_index,
-                   slot_count, spread, wrap_points, what_grid)
+from .nfft import (PATTERN_2M2, PATTERN_PAPER, coeffs_to_grid, grid_to_coeffs, interpolate, point_slots,
+                   reduce_index, slot_count, spread, wrap_points, what_grid)
 
 
 def column_members(x: np.ndarray, Ms: int, m: int, pattern=PATTERN_2M2):
@@ -160,6 +161,23 @@ def reconstruct(x: np.ndarray, f: np.ndarray, coeff: np.ndarray, M: int, sigma: 
     return (gh / what_grid(kind, M, Ms, m, d)).ravel()
 
 
+def inverse_adjoint(x: np.ndarray, h: np.ndarray, coeff: np.ndarray, M: int, sigma: float, m: int,
+                    kind: str = W.KB, pattern=PATTERN_2M2) -> np.ndarray:
+    """Remark 4.6: the inverse adjoint NFFT f = B_opt F D h, an approximate solution of
+    A^* f = h (eq. problem_infft*) for |I_M| <= N.
+
+    The same steps as Algorithm 2.1 (division by |I_Ms| w^(k), zero padding, DFT with
+    sign +) with the window entries of B replaced by the optimised entries B_opt[j, l]
+    (not conjugated)."""
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    d = x.shape[1]
+    Ms = W.oversampled_size(M, sigma)
+    gh = np.asarray(h, dtype=np.complex128).reshape((M,) * d) / what_grid(kind, M, Ms, m, d)
+    g = coeffs_to_grid(gh, Ms) / Ms ** d
+    cand, valid = point_slots(x, Ms, m, pattern)
+    return interpolate(g, x, Ms, m, coeff, cand, valid)
+
+
 def frobenius_error(x: np.ndarray, M: int, sigma: float, m: int, kind_D: str, B: np.ndarray) -> float:
     """|| A^* B F D - I ||_F (eq. matrixnorms_2d) with explicit matrices."""
     from .fourier import matrix_A
@@ -180,5 +198,5 @@ def column_residual_of(B_col_vals: np.ndarray, x_members: np.ndarray, l: np.ndar
 
 
 __all__ = ["column_members", "column_l", "matrix_H", "rhs", "gram_closed_form", "rhs_closed_form",
-           "solve_column", "optimize_B", "reconstruct", "frobenius_error", "column_residual_of",
+           "solve_column", "optimize_B", "reconstruct", "inverse_adjoint", "frobenius_error", "column_residual_of",
            "PATTERN_2M2", "PATTERN_PAPER", "wrap_points"]

@@ -108,3 +108,47 @@ def test_real_field_variant_is_no_better_than_complex():
     scale = np.sum(W.what(W.KB, FO.index_set(M, 2), M, Ms, m) ** 2)   # ||rhs||^2
     for col in e_c:
         assert e_c[col] <= e_r[col] + 1e-12 * scale
+
+
+# --- inverse adjoint NFFT (Remark 4.6) --------------------------------------------------
+
+def test_inverse_adjoint_is_the_product_B_F_D():
+    """f = B_opt F D h with the explicit factor matrices (eq. matrix_F, eq. matrix_D,
+    B_opt placed by eq. matrix_B)."""
+    x, M, sigma, m, Ms = _setup(N=80, M=4, m=2)
+    for pattern in (BO.PATTERN_2M2, BO.PATTERN_PAPER):
+        coeff, _ = BO.optimize_B(x, M, sigma, m, W.KB, pattern)
+        h = inputs.coeffs_complex((M * M,), 91)
+        f = BO.inverse_adjoint(x, h, coeff, M, sigma, m, W.KB, pattern)
+        B = NF.matrix_B(x, M, Ms, m, W.KB, pattern, coeff=coeff)
+        f_ref = B @ NF.matrix_F(M, Ms, 2) @ NF.matrix_D(M, Ms, m, 2, W.KB) @ h
+        assert np.allclose(f, f_ref, rtol=0, atol=1e-12 * np.abs(f_ref).max())
+
+
+def test_inverse_adjoint_is_the_adjoint_of_algorithm_4_4():
+    """<D^*F^*B^* f, h> = <f, B F D h> for any f, h: the two share B_opt."""
+    x, M, sigma, m, Ms = _setup(N=120, M=6, m=2)
+    coeff, _ = BO.optimize_B(x, M, sigma, m, W.KB, BO.PATTERN_2M2)
+    f = inputs.samples_complex(x.shape[0], 92)
+    h = inputs.coeffs_complex((M * M,), 93)
+    lhs = np.vdot(BO.reconstruct(x, f, coeff, M, sigma, m, W.KB, BO.PATTERN_2M2), h)
+    rhs = np.vdot(f, BO.inverse_adjoint(x, h, coeff, M, sigma, m, W.KB, BO.PATTERN_2M2))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+@pytest.mark.parametrize("kind", [W.KB, W.DIRICHLET])
+def test_inverse_adjoint_residual_within_frobenius_bound(kind):
+    """A^* f - h = (A^* B_opt F D - I) h, so ||A^* f - h|| <= ||A^* B_opt F D - I||_F ||h||
+    (eq. problem_infft*, Remark 4.6), and the optimised B does better than the window's."""
+    x, M, sigma, m, Ms = _setup(N=200, M=6, m=2)
+    coeff, _ = BO.optimize_B(x, M, sigma, m, kind, BO.PATTERN_2M2)
+    h = inputs.coeffs_complex((M * M,), 94)
+    f = BO.inverse_adjoint(x, h, coeff, M, sigma, m, kind, BO.PATTERN_2M2)
+    res = np.linalg.norm(FO.adjoint_ndft(x, f, M) - h)
+    # with coeff given, matrix_B takes only the slot positions from the window
+    B = NF.matrix_B(x, M, Ms, m, W.KB, BO.PATTERN_2M2, coeff=coeff)
+    fro = BO.frobenius_error(x, M, sigma, m, kind, B)
+    assert res <= fro * np.linalg.norm(h)
+    if kind == W.KB:
+        f0 = NF.nfft(x, h, M, sigma, m, kind)          # the window's B, same F and D
+        assert res < np.linalg.norm(FO.adjoint_ndft(x, f0, M) - h)
