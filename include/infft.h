@@ -189,6 +189,17 @@ infft_status infft_adjoint(infft_plan_t plan, int mode, const void* f, void* fha
 infft_status infft_forward(infft_plan_t plan, const void* fhat, void* f, void* stream);
 
 /*
+ * infft_inverse_adjoint -- the inverse adjoint NFFT of Remark 4.6: an approximate
+ * solution f of A^* f = h (eq. problem_infft*, |I_M| <= N), f = B_opt F D h.  The steps of
+ * Algorithm 2.1 with the window entries of B replaced by the plan's optimised entries
+ * B_opt[j, l] (not conjugated), D built from the window B_opt was optimised for.
+ *   h : M^d complex (host or device), C order over I_M, as fhat elsewhere.
+ *   f : N complex (host or device), the caller's point order.
+ * Needs infft_optimize_B first (else INFFT_ESTATE).  Stream ordered like infft_forward.
+ */
+infft_status infft_inverse_adjoint(infft_plan_t plan, const void* h, void* f, void* stream);
+
+/*
  * infft_adjoint_batched -- `count` reconstructions on (possibly different) plans
  * of the same d and precision, executed as one launch per kernel stage over
  * all of them.  f[i], fhat[i] are device pointers, or host pointers staged through

@@ -47,6 +47,7 @@ _SIGS = {
     "infft_get_bopt": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "infft_adjoint": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "infft_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "infft_inverse_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "infft_adjoint_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p),
                                         C.POINTER(C.c_void_p), C.c_void_p]),
     "infft_adjoint_batched_slots": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p),
@@ -270,6 +271,17 @@ class Plan:
                 fhat = torch.empty((self.M,) * self.d, dtype=f.dtype, device=f.device)
         _check(infft_adjoint(self.handle, mode, _ptr(f), _ptr(fhat), _stream(stream)))
         return fhat
+
+    def inverse_adjoint(self, h, f=None, stream=None):
+        """f = B_opt F D h (Remark 4.6), an approximate solution of A^* f = h; needs optimize_B."""
+        if f is None:
+            if isinstance(h, np.ndarray):
+                f = np.empty(self.N, dtype=self.complex_dtype)
+            else:
+                import torch
+                f = torch.empty(self.N, dtype=h.dtype, device=h.device)
+        _check(load().infft_inverse_adjoint(self.handle, _ptr(h), _ptr(f), _stream(stream)))
+        return f
 
     def forward(self, fhat, f=None, stream=None):
         if f is None:

@@ -132,7 +132,7 @@ static bool interp_t_eligible(const JobSet<R>& js, int* m_out) {
     const int m = js.job[0].m;
     for (int j = 0; j < js.njobs; ++j) {
         const Job<R>& J = js.job[j];
-        if (J.m != m || (J.T & (J.T - 1)) != 0 || (J.Ms & (J.Ms - 1)) != 0) return false;
+        if (J.m != m || J.mode == INFFT_MODE_BOPT || (J.T & (J.T - 1)) != 0 || (J.Ms & (J.Ms - 1)) != 0) return false;
     }
     // float64 d = 2 up to the CG's m = 8; otherwise m <= 6
     if (m < 1 || m > ((D == 2 && sizeof(R) == 8) ? 8 : 6)) return false;

@@ -379,6 +379,8 @@ __global__ void __launch_bounds__(128) k_interp(const __grid_constant__ JobSet<R
     const int4 item = J.items[gitem - js.pre_items[jb]];
     const int P = J.P, m = J.m, Ms = J.Ms, T = J.T;
     const int W = 2 * m + 1;
+    const bool bopt = (J.mode == INFFT_MODE_BOPT);   // f = B_opt F D h (Remark 4.6)
+    const int S = bopt ? J.S : W;                     // slots per axis
     const int cells = ipow(P, D);
     unsigned char* base = smem_raw + (size_t)warp * js.smem_per_warp;
     cx<R>* pad = reinterpret_cast<cx<R>*>(base);
@@ -403,7 +405,7 @@ __global__ void __launch_bounds__(128) k_interp(const __grid_constant__ JobSet<R
     int pstride[D];
     pstride[D - 1] = 1;
     for (int t = D - 2; t >= 0; --t) pstride[t] = pstride[t + 1] * P;
-    const int ntap = ipow(W, D);
+    const int ntap = ipow(S, D);
     __syncwarp();
 
     for (int c0 = 0; c0 < item.z; c0 += 32) {
@@ -418,23 +420,30 @@ __global__ void __launch_bounds__(128) k_interp(const __grid_constant__ JobSet<R
                 o[t] = c - tt[t] * T;
             }
             R* ps = psi + lane * D * W;
-            for (int t = 0; t < D; ++t) {
-                const R u = J.u[(size_t)i * D + t];
-                for (int s = 0; s < W; ++s) ps[t * W + s] = tap_weight<R>(J.window, u, s, m, J.inv_m, J.beta);
+            if (!bopt) {
+                for (int t = 0; t < D; ++t) {
+                    const R u = J.u[(size_t)i * D + t];
+                    for (int s = 0; s < W; ++s) ps[t * W + s] = tap_weight<R>(J.window, u, s, m, J.inv_m, J.beta);
+                }
             }
+            const cx<R>* cf = bopt ? J.coef + (size_t)i * ntap : nullptr;
             cx<R> acc = mk<R>(0, 0);
             for (int q = 0; q < ntap; ++q) {
                 int r2 = q, idx = 0;
                 R wgt = R(1);
                 for (int t = D - 1; t >= 0; --t) {
-                    const int s = r2 % W;
-                    r2 /= W;
+                    const int s = r2 % S;
+                    r2 /= S;
                     idx += (o[t] + s) * pstride[t];
-                    wgt *= ps[t * W + s];
+                    if (!bopt) wgt *= ps[t * W + s];
                 }
                 const cx<R> g = pad[idx];
-                acc.re += wgt * g.re;
-                acc.im += wgt * g.im;
+                if (bopt) {
+                    acc = add(acc, mul(cf[q], g));   // B_opt[j, l] g_l
+                } else {
+                    acc.re += wgt * g.re;
+                    acc.im += wgt * g.im;
+                }
             }
             J.out[__ldg(J.perm + i)] = acc;
         }

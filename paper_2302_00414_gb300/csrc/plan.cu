@@ -509,7 +509,7 @@ static infft_status ensure_io(infft_plan_s* p) {
 
 static infft_status transform(infft_plan_t p, int mode, const void* in, void* out, void* stream, bool forward) {
     if (!p || !in || !out) { set_error("null argument"); return INFFT_EINVAL; }
-    if (!forward) INFFT_TRY(check_mode(p, mode));
+    if (!forward || mode == INFFT_MODE_BOPT) INFFT_TRY(check_mode(p, mode));
     else if (p->window == WK_DIRICHLET) { set_error("no forward NFFT with the Dirichlet window"); return INFFT_ESTATE; }
     cudaStream_t st = (cudaStream_t)stream;
     const size_t C = p->fp64 ? 16 : 8;
@@ -546,6 +546,10 @@ infft_status infft_adjoint(infft_plan_t p, int mode, const void* f, void* fhat, 
 
 infft_status infft_forward(infft_plan_t p, const void* fhat, void* f, void* stream) {
     return transform(p, INFFT_MODE_PLAIN, fhat, f, stream, true);
+}
+
+infft_status infft_inverse_adjoint(infft_plan_t p, const void* h, void* f, void* stream) {
+    return transform(p, INFFT_MODE_BOPT, h, f, stream, true);
 }
 
 static infft_status batched_jobs_check(const infft_plan_t* plans, int count, int mode) {

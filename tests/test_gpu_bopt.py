@@ -88,3 +88,52 @@ def test_bopt_improves_on_window_and_bound():
     assert np.linalg.norm(h - fh.ravel()) ** 2 <= eps * np.sum(wh ** -2.0) * np.linalg.norm(fh) ** 2
     h0 = p.adjoint(to_dev(torch, f)).cpu().numpy().ravel()  # plain adjoint NFFT
     assert np.linalg.norm(h - fh.ravel()) < np.linalg.norm(h0 - fh.ravel())
+
+
+# --- inverse adjoint NFFT (Remark 4.6) --------------------------------------------------
+
+@pytest.mark.parametrize("window,pattern", [("kb", "2m+2"), ("kb", "paper"), ("dirichlet", "2m+2"),
+                                            ("bspline", "paper")])
+def test_inverse_adjoint_matches_oracle(window, pattern):
+    """f = B_opt F D h on the GPU against the oracle's with its own B_opt (well-conditioned
+    columns, so both B_opt agree to about 1e-11)."""
+    L, torch = lib_or_skip()
+    d, M, N, m = 2, 8, 150, 2
+    x = inputs.random_points(N, d, 5)
+    h = inputs.coeffs_complex((M, M), 95)
+    c_ref, _ = BO.optimize_B(x, M, 2.0, m, window, pattern)
+    ref = BO.inverse_adjoint(x, h.ravel(), c_ref, M, 2.0, m, window, pattern)
+    for prec, tol in (("fp64", 1e-9), ("fp32", 1e-5)):
+        p = L.Plan(x, M, 2.0, m, prec, window=window)
+        p.optimize_B(PAT[pattern])
+        cd = torch.complex128 if prec == "fp64" else torch.complex64
+        f = p.inverse_adjoint(to_dev(torch, h, cd)).cpu().numpy()
+        assert rel(f, ref) < tol
+        # host buffers give the same result
+        f_host = p.inverse_adjoint(h.astype(np.complex128 if prec == "fp64" else np.complex64))
+        assert np.array_equal(f_host, f)
+
+
+def test_inverse_adjoint_solves_the_adjoint_problem():
+    """The residual of A^* f = h (eq. problem_infft*) with B_opt is below the window's
+    (f = B F D h, the plain NFFT), also in one and three dimensions; the oracle's pins bound
+    it by ||A^* B_opt F D - I||_F ||h||."""
+    L, torch = lib_or_skip()
+    for d, M, N, m in ((1, 16, 64, 3), (2, 8, 200, 2), (3, 4, 300, 1)):
+        x = inputs.random_points(N, d, 40 + d)
+        h = inputs.coeffs_complex((M,) * d, 96)
+        p = L.Plan(x, M, 2.0, m, "fp64")
+        p.optimize_B()
+        f = p.inverse_adjoint(to_dev(torch, h)).cpu().numpy()
+        res = np.linalg.norm(FO.adjoint_ndft(x, f, M) - h.ravel())
+        f0 = p.forward(to_dev(torch, h)).cpu().numpy()
+        res0 = np.linalg.norm(FO.adjoint_ndft(x, f0, M) - h.ravel())
+        assert res < res0
+
+
+def test_inverse_adjoint_needs_bopt():
+    L, torch = lib_or_skip()
+    x = inputs.random_points(100, 2, 3)
+    p = L.Plan(x, 8, 2.0, 2, "fp64")
+    with pytest.raises(L.InfftError):
+        p.inverse_adjoint(to_dev(torch, inputs.coeffs_complex((8, 8), 1)))
