@@ -70,7 +70,8 @@ enum {
     INFFT_FP64 = 2,          /* everything in float64 */
     INFFT_WIN_KB = 0,        /* Kaiser-Bessel window (default) */
     INFFT_WIN_BSPLINE = 4,   /* B-spline window B_{2m}(M_sigma x), eq. window_bspline */
-    INFFT_WIN_DIRICHLET = 8  /* asymmetric Dirichlet window (B_opt only, Theorem 4.5) */
+    INFFT_WIN_DIRICHLET = 8, /* asymmetric Dirichlet window (B_opt only, Theorem 4.5) */
+    INFFT_POOLED = 16        /* plan memory from the library's stream-ordered pool (see infft_plan) */
 };
 
 /* reconstruction modes of infft_adjoint */
@@ -103,12 +104,21 @@ enum {
  *   sigma  : oversampling factor >= 1; M_sigma = 2 ceil(ceil(sigma M)/2) must be a
  *            power of two <= 4096 (else INFFT_EUNSUPPORTED).
  *   m      : truncation parameter, 1 <= m, 2m+2 <= M_sigma.
- *   flags  : INFFT_FP32 or INFFT_FP64, or-ed with a window flag.
+ *   flags  : INFFT_FP32 or INFFT_FP64, or-ed with a window flag and optionally INFFT_POOLED.
  *   stream : stream for the set-up kernels (the call synchronises it).
  *   out    : receives the plan.
  * Sorts the points into tiles of the oversampled grid (counting sort over
  * grid cells, deterministic order), builds the work lists and the tables of
  * 1/(M_sigma w^(k)) (eq. matrix_D) and FFT twiddles.
+ *
+ * Memory.  By default a plan's device buffers come from cudaMalloc and go back by
+ * cudaFree; both synchronise the device with work that other host threads have queued.
+ * With INFFT_POOLED they come from a stream-ordered pool the library owns per device,
+ * allocated in the order of the stream of the call that needs them (creation, later
+ * batched calls, weights, B_opt) and returned in infft_destroy after a device
+ * synchronisation; freed blocks stay in the pool for reuse until the process exits.
+ * Meant for servers that build plans on one thread while another launches
+ * reconstructions.
  */
 infft_status infft_plan(int d, int M, int64_t N, const double* x, double sigma, int m,
                         unsigned flags, void* stream, infft_plan_t* out);

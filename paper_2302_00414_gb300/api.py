@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(HERE, "libinfft.so")
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ETIMEOUT, ESTATE, EUNSUPPORTED = range(8)
 FP32, FP64 = 1, 2
 WIN_KB, WIN_BSPLINE, WIN_DIRICHLET = 0, 4, 8
+POOLED = 16
 MODE_PLAIN, MODE_DCF, MODE_BOPT = 0, 1, 2
 BOPT_PATTERN_2M2, BOPT_PATTERN_PAPER, BOPT_REAL = 0, 1, 2
 WEIGHTS_AUTO, WEIGHTS_NFFT, WEIGHTS_TOEPLITZ = 0, 1, 2
@@ -191,9 +192,9 @@ class Plan:
     """A plan for fixed points x (N x d, float64 numpy array or torch tensor)."""
 
     def __init__(self, x, M: int, sigma: float = 2.0, m: int = 4, precision: str = "fp32",
-                 window: str = "kb", stream=None):
+                 window: str = "kb", stream=None, pooled: bool = False):
         self.precision = precision
-        flags = {"fp32": FP32, "fp64": FP64}[precision]
+        flags = {"fp32": FP32, "fp64": FP64}[precision] | (POOLED if pooled else 0)
         flags |= {"kb": WIN_KB, "bspline": WIN_BSPLINE, "dirichlet": WIN_DIRICHLET}[window]
         if isinstance(x, np.ndarray):
             x = np.ascontiguousarray(x, dtype=np.float64)

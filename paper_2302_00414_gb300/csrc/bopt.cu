@@ -376,8 +376,8 @@ static infft_status optimize_impl(infft_plan_s* p, unsigned opts, double* max_re
     // largest column, ||rhs||^2 = sum_k w^(k)^2 = prod_t sum_{k_t} w^(k_t)^2
     std::vector<int> hs(ncols + 1);
     std::vector<double> hw(g.M);
-    INFFT_CUDA(cudaMemcpyAsync(hs.data(), start, (ncols + 1) * 4, cudaMemcpyDeviceToHost, st));
-    INFFT_CUDA(cudaMemcpyAsync(hw.data(), what1, g.M * 8, cudaMemcpyDeviceToHost, st));
+    INFFT_TRY(read_back(hs.data(), start, (ncols + 1) * 4, st));
+    INFFT_TRY(read_back(hw.data(), what1, g.M * 8, st));
     INFFT_CUDA(cudaStreamSynchronize(st));
     int n_max = 1;
     for (long long c = 0; c < ncols; ++c) n_max = std::max(n_max, hs[c + 1] - hs[c]);
@@ -412,8 +412,8 @@ static infft_status optimize_impl(infft_plan_s* p, unsigned opts, double* max_re
     INFFT_LAUNCHED();
     double mres = 0;
     int nfail = 0;
-    INFFT_CUDA(cudaMemcpyAsync(&mres, scal, 8, cudaMemcpyDeviceToHost, st));
-    INFFT_CUDA(cudaMemcpyAsync(&nfail, status, 4, cudaMemcpyDeviceToHost, st));
+    INFFT_TRY(read_back(&mres, scal, 8, st));
+    INFFT_TRY(read_back(&nfail, status, 4, st));
     INFFT_CUDA(cudaStreamSynchronize(st));
     if (max_res) *max_res = mres;
     p->has_bopt = true;
@@ -435,6 +435,7 @@ infft_status infft_optimize_B(infft_plan_t p, unsigned opts, double* max_col_res
     if (!p) { set_error("null plan"); return INFFT_EINVAL; }
     if (opts & ~3u) { set_error("unknown options %u", opts); return INFFT_EINVAL; }
     std::vector<void*> tmp;
+    p->pool_stream = (cudaStream_t)stream;
     infft_status s = optimize_impl(p, opts, max_col_residual, (cudaStream_t)stream, tmp);
     cudaStreamSynchronize((cudaStream_t)stream);
     for (void* q : tmp) cudaFree(q);

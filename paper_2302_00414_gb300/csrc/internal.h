@@ -62,6 +62,10 @@ struct infft_plan_s {
     void* io_out = nullptr;
 
     size_t device_bytes = 0;
+    // plans made inside the library (the weights' degree-2M plan) allocate from the
+    // library's stream-ordered pool on this stream and free the same way
+    bool pooled = false;
+    cudaStream_t pool_stream = nullptr;
 };
 
 struct infft_batch_s {
@@ -72,6 +76,24 @@ struct infft_batch_s {
 };
 
 namespace infft {
+
+// Stream-ordered device memory from a pool the library owns per device (its release
+// threshold is unlimited, so freed blocks are kept for reuse).  Neither call synchronises
+// the device, unlike cudaMalloc / cudaFree, so a thread building plans or weights does not
+// hold up other threads' launches.  Memory is usable in stream order on `st`.
+infft_status pool_alloc(void** ptr, size_t bytes, cudaStream_t st);
+void pool_free(void* ptr, cudaStream_t st);
+
+// Copy device -> pageable host memory after the stream has drained: a pageable copy
+// waits for the stream's earlier work inside the driver and holds up the other host
+// threads' CUDA calls meanwhile; synchronising first leaves only the short copy.
+infft_status read_back(void* dst, const void* src, size_t bytes, cudaStream_t st);
+
+// create a plan (argument checks of infft_plan); pooled plans use pool_alloc on `stream`
+infft_status plan_create(int d, int M, int64_t N, const double* x, double sigma, int m, unsigned flags,
+                         cudaStream_t stream, bool pooled, infft_plan_s** out);
+// free a plan's memory without a device-wide synchronisation (pooled plans: in stream order)
+void plan_release(infft_plan_s* p);
 
 // thread-local error message and launch counter
 void set_error(const char* fmt, ...);

@@ -1,6 +1,7 @@
 // Plan creation (point binning, tables) and the C-ABI entry points of the
 // transforms (Algorithms 2.1, 2.4, 3.7, 4.4).
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -25,9 +26,58 @@ void set_error(const char* fmt, ...) {
 }
 void count_launch(int n) { g_launches += (uint64_t)n; }
 
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64] = {};
+
+infft_status pool_alloc(void** ptr, size_t bytes, cudaStream_t st) {
+    *ptr = nullptr;
+    int dev = 0;
+    INFFT_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) { set_error("device %d out of range", dev); return INFFT_EINVAL; }
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (!g_pool[dev]) {
+            cudaMemPoolProps props;
+            memset(&props, 0, sizeof(props));
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            INFFT_CUDA(cudaMemPoolCreate(&g_pool[dev], &props));
+            uint64_t keep = UINT64_MAX;
+            INFFT_CUDA(cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep));
+        }
+        pool = g_pool[dev];
+    }
+    cudaError_t e = cudaMallocFromPoolAsync(ptr, std::max<size_t>(bytes, 16), pool, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        set_error("pool allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        return INFFT_ENOMEM;
+    }
+    return INFFT_OK;
+}
+
+infft_status read_back(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    INFFT_CUDA(cudaStreamSynchronize(st));
+    INFFT_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st));
+    INFFT_CUDA(cudaStreamSynchronize(st));
+    return INFFT_OK;
+}
+
+void pool_free(void* ptr, cudaStream_t st) {
+    if (ptr) cudaFreeAsync(ptr, st);
+}
+
 infft_status dev_alloc(infft_plan_s* p, void** ptr, size_t bytes) {
     *ptr = nullptr;
     if (bytes == 0) return INFFT_OK;
+    if (p && p->pooled) {
+        INFFT_TRY(pool_alloc(ptr, bytes, p->pool_stream));
+        p->device_bytes += bytes;
+        return INFFT_OK;
+    }
     cudaError_t e = cudaMalloc(ptr, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -276,12 +326,14 @@ static void free_plan(infft_plan_s* p) {
                     p->dinv_win, p->w_master, p->w_sorted, p->coef, p->coef64, p->padded, p->grid, p->tmp1,
                     p->tmp2, p->io_in, p->io_out, p->wpoly};
     for (void* q : ptrs)
-        if (q) cudaFree(q);
+        if (q) { if (p->pooled) pool_free(q, p->pool_stream); else cudaFree(q); }
     for (const auto& e : p->extra)
         for (void* q : e)
-            if (q) cudaFree(q);
+            if (q) { if (p->pooled) pool_free(q, p->pool_stream); else cudaFree(q); }
     delete p;
 }
+
+void plan_release(infft_plan_s* p) { free_plan(p); }
 
 static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
@@ -314,18 +366,18 @@ static infft_status build_plan(infft_plan_s* p, const double* x_in, cudaStream_t
     // points to the device
     double* x_dev = nullptr;
     const bool x_on_dev = is_device_pointer(x_in);
-    INFFT_CUDA(cudaMalloc((void**)&x_dev, (size_t)N * d * sizeof(double)));
+    INFFT_TRY(pool_alloc((void**)&x_dev, (size_t)N * d * sizeof(double), st));
     INFFT_CUDA(cudaMemcpyAsync(x_dev, x_in, (size_t)N * d * sizeof(double),
                                x_on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     uint32_t *key = nullptr, *cellrm = nullptr;
     double *u64 = nullptr, *xw = nullptr;
     int *count = nullptr, *fill = nullptr, *order = nullptr;
-    INFFT_CUDA(cudaMalloc((void**)&key, (size_t)N * 4));
-    INFFT_CUDA(cudaMalloc((void**)&cellrm, (size_t)N * 4));
-    INFFT_CUDA(cudaMalloc((void**)&u64, (size_t)N * d * 8));
-    INFFT_CUDA(cudaMalloc((void**)&xw, (size_t)N * d * 8));
-    INFFT_CUDA(cudaMalloc((void**)&fill, (size_t)(nkeys + 1) * 4));
-    INFFT_CUDA(cudaMalloc((void**)&order, (size_t)N * 4));
+    INFFT_TRY(pool_alloc((void**)&key, (size_t)N * 4, st));
+    INFFT_TRY(pool_alloc((void**)&cellrm, (size_t)N * 4, st));
+    INFFT_TRY(pool_alloc((void**)&u64, (size_t)N * d * 8, st));
+    INFFT_TRY(pool_alloc((void**)&xw, (size_t)N * d * 8, st));
+    INFFT_TRY(pool_alloc((void**)&fill, (size_t)(nkeys + 1) * 4, st));
+    INFFT_TRY(pool_alloc((void**)&order, (size_t)N * 4, st));
     INFFT_TRY(dev_alloc(p, (void**)&p->cell_start, (size_t)(nkeys + 1) * 4));
     count = p->cell_start;
     INFFT_CUDA(cudaMemsetAsync(count, 0, (size_t)(nkeys + 1) * 4, st));
@@ -359,7 +411,7 @@ static infft_status build_plan(infft_plan_s* p, const double* x_in, cudaStream_t
     for (int t = 0; t < d; ++t) { tpow *= p->T; ntl *= p->ntile; }
     const int ntiles = (int)ntl;  // nkeys = ntiles * tpow
     std::vector<int> cs(nkeys + 1);
-    INFFT_CUDA(cudaMemcpyAsync(cs.data(), count, (size_t)(nkeys + 1) * 4, cudaMemcpyDeviceToHost, st));
+    INFFT_TRY(read_back(cs.data(), count, (size_t)(nkeys + 1) * 4, st));
     INFFT_CUDA(cudaStreamSynchronize(st));
     // d = 1: short items so that a few hundred points still spread on several warps
     const int cap = d == 1 ? 32 : 512;
@@ -375,10 +427,12 @@ static infft_status build_plan(infft_plan_s* p, const double* x_in, cudaStream_t
     INFFT_TRY(dev_alloc(p, (void**)&p->items, std::max<size_t>(1, items.size()) * sizeof(int4)));
     INFFT_TRY(dev_alloc(p, (void**)&p->tile_items, (size_t)(ntiles + 1) * 4));
     if (!items.empty())
-        INFFT_CUDA(cudaMemcpy(p->items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
-    INFFT_CUDA(cudaMemcpy(p->tile_items, tile_items.data(), (size_t)(ntiles + 1) * 4, cudaMemcpyHostToDevice));
+        INFFT_CUDA(cudaMemcpyAsync(p->items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    INFFT_CUDA(cudaMemcpyAsync(p->tile_items, tile_items.data(), (size_t)(ntiles + 1) * 4, cudaMemcpyHostToDevice,
+                               st));
 
-    cudaFree(x_dev); cudaFree(key); cudaFree(cellrm); cudaFree(u64); cudaFree(xw); cudaFree(fill); cudaFree(order);
+    for (void* q : {(void*)x_dev, (void*)key, (void*)cellrm, (void*)u64, (void*)xw, (void*)fill, (void*)order})
+        pool_free(q, st);
 
     // tables
     INFFT_TRY(dev_alloc(p, &p->dinv, (size_t)p->M * R_sz));
@@ -420,18 +474,8 @@ static infft_status build_plan(infft_plan_s* p, const double* x_in, cudaStream_t
     return INFFT_OK;
 }
 
-}  // namespace infft
-
-using namespace infft;
-
-extern "C" {
-
-const char* infft_last_error(void) { return g_err; }
-uint64_t infft_launch_count(void) { return g_launches; }
-void infft_launch_count_reset(void) { g_launches = 0; }
-
-infft_status infft_plan(int d, int M, int64_t N, const double* x, double sigma, int m, unsigned flags, void* stream,
-                        infft_plan_t* out) {
+infft_status plan_create(int d, int M, int64_t N, const double* x, double sigma, int m, unsigned flags,
+                         cudaStream_t stream, bool pooled, infft_plan_s** out) {
     if (!out) { set_error("out is NULL"); return INFFT_EINVAL; }
     *out = nullptr;
     if (d < 1 || d > 3 || M < 2 || (M & 1) || N < 1 || N >= (1ll << 31) || !x || !(sigma >= 1.0) || m < 1) {
@@ -451,15 +495,33 @@ infft_status infft_plan(int d, int M, int64_t N, const double* x, double sigma, 
     int l = 0;
     while ((1 << l) < Ms) ++l;
     p->logMs = l;
-    infft_status s = build_plan(p, x, (cudaStream_t)stream);
+    p->pooled = pooled || (flags & INFFT_POOLED) != 0;
+    p->pool_stream = stream;
+    infft_status s = build_plan(p, x, stream);
     if (s != INFFT_OK) { free_plan(p); return s; }
     *out = p;
     return INFFT_OK;
 }
 
+}  // namespace infft
+
+using namespace infft;
+
+extern "C" {
+
+const char* infft_last_error(void) { return g_err; }
+uint64_t infft_launch_count(void) { return g_launches; }
+void infft_launch_count_reset(void) { g_launches = 0; }
+
+infft_status infft_plan(int d, int M, int64_t N, const double* x, double sigma, int m, unsigned flags, void* stream,
+                        infft_plan_t* out) {
+    return plan_create(d, M, N, x, sigma, m, flags, (cudaStream_t)stream, false, out);
+}
+
 void infft_destroy(infft_plan_t p) {
     if (!p) return;
     cudaDeviceSynchronize();
+    p->pool_stream = 0;   // pooled memory goes back to the pool; every use has completed
     free_plan(p);
 }
 
@@ -518,6 +580,7 @@ static infft_status transform(infft_plan_t p, int mode, const void* in, void* ou
     const bool in_dev = is_device_pointer(in), out_dev = is_device_pointer(out);
     const void* din = in;
     void* dout = out;
+    p->pool_stream = st;
     if (!in_dev || !out_dev) INFFT_TRY(ensure_io(p));
     if (!in_dev) {
         INFFT_CUDA(cudaMemcpyAsync(p->io_in, in, nin * C, cudaMemcpyHostToDevice, st));
@@ -570,7 +633,9 @@ static infft_status batched_jobs_check(const infft_plan_t* plans, int count, int
 // Host buffers are staged through the plan's I/O buffers, so a plan given a host
 // pointer may appear only once.  Allocates, so it runs before a graph capture begins.
 static infft_status prepare_batched(const infft_plan_t* plans, int count, const void* const* f,
-                                    void* const* fhat, const int* slots_in, std::vector<int>& slot) {
+                                    void* const* fhat, const int* slots_in, std::vector<int>& slot,
+                                    cudaStream_t st) {
+    for (int i = 0; i < count; ++i) plans[i]->pool_stream = st;   // pooled plans allocate in this order
     slot.assign(count, 0);
     for (int i = 0; i < count; ++i) {
         if (slots_in) {
@@ -598,11 +663,12 @@ static infft_status prepare_batched(const infft_plan_t* plans, int count, const 
             INFFT_TRY(ensure_io(plans[i]));
         }
         infft_plan_s* p = plans[i];
-        while ((int)p->extra.size() < slot[i]) {
-            std::array<void*, 4> e{nullptr, nullptr, nullptr, nullptr};
-            p->extra.push_back(e);
+        if (slot[i] > 0) {   // allocate only the sets that are used
+            if ((int)p->extra.size() < slot[i])
+                p->extra.resize(slot[i], std::array<void*, 4>{nullptr, nullptr, nullptr, nullptr});
+            std::array<void*, 4>& e = p->extra[slot[i] - 1];
             for (int q = 0; q < 4; ++q)
-                if (p->scratch_bytes[q]) INFFT_TRY(dev_alloc(p, &p->extra.back()[q], p->scratch_bytes[q]));
+                if (p->scratch_bytes[q] && !e[q]) INFFT_TRY(dev_alloc(p, &e[q], p->scratch_bytes[q]));
         }
     }
     return INFFT_OK;
@@ -612,7 +678,7 @@ static infft_status run_batched(const infft_plan_t* plans, int count, int mode, 
                                 void* const* fhat, cudaStream_t st, cudaEvent_t* ev = nullptr,
                                 const int* slots_in = nullptr) {
     std::vector<int> slot;
-    INFFT_TRY(prepare_batched(plans, count, f, fhat, slots_in, slot));
+    INFFT_TRY(prepare_batched(plans, count, f, fhat, slots_in, slot, st));
     std::vector<const void*> fin(count);
     std::vector<void*> fout(count);
     bool any_host_out = false;
@@ -694,7 +760,7 @@ infft_status infft_batch_create(const infft_plan_t* plans, int count, int mode, 
     if (!f || !fhat) { set_error("null buffers"); return INFFT_EINVAL; }
     {
         std::vector<int> slot;   // allocations happen outside the capture
-        INFFT_TRY(prepare_batched(plans, count, f, fhat, nullptr, slot));
+        INFFT_TRY(prepare_batched(plans, count, f, fhat, nullptr, slot, (cudaStream_t)stream));
     }
     cudaStream_t cap;
     INFFT_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));

@@ -308,13 +308,13 @@ static infft_status ensure_weight_buffers(infft_plan_s* p) {
 
 static infft_status weights_impl(infft_plan_s* p, int max_iter, double rel_tol, int m_cg, unsigned opts,
                                  double* residual_inf, int* iters_out, cudaStream_t st, std::vector<void*>& tmp,
-                                 infft_plan_t& sub) {
+                                 infft_plan_s*& sub) {
     const int d = p->d, M2 = 2 * p->M;
     const int N = (int)p->N;
     if (m_cg <= 0) m_cg = (d <= 2) ? 8 : 4;
     const int Ms2 = 2 * M2;
     m_cg = std::min(m_cg, (Ms2 - 2) / 2);
-    INFFT_TRY(infft_plan(d, M2, N, p->x64, 2.0, m_cg, INFFT_FP64 | INFFT_WIN_KB, st, &sub));
+    INFFT_TRY(plan_create(d, M2, N, p->x64, 2.0, m_cg, INFFT_FP64 | INFFT_WIN_KB, st, true, &sub));
     long long K = 1;
     for (int t = 0; t < d; ++t) K *= M2;
     const bool second_kind = K <= N;
@@ -327,9 +327,10 @@ static infft_status weights_impl(infft_plan_s* p, int max_iter, double rel_tol, 
     const bool toeplitz = toeplitz_ok && !(opts & INFFT_WEIGHTS_NFFT);
     const long long n = second_kind ? K : N;   // CG unknowns
     const long long aux_n = second_kind ? N : K;
+    // temporaries from the library's stream-ordered pool: no device-wide synchronisation
     auto alloc = [&](size_t bytes) -> void* {
         void* q = nullptr;
-        if (cudaMalloc(&q, bytes) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+        if (pool_alloc(&q, bytes, st) != INFFT_OK) return nullptr;
         tmp.push_back(q);
         return q;
     };
@@ -366,7 +367,7 @@ static infft_status weights_impl(infft_plan_s* p, int max_iter, double rel_tol, 
     INFFT_TRY(dot(r, r, n, part, sc + 0, st));  // rr
     INFFT_CUDA(cudaMemcpyAsync(bn, sc + 0, 8, cudaMemcpyDeviceToDevice, st));
     double b2 = 0;
-    INFFT_CUDA(cudaMemcpyAsync(&b2, bn, 8, cudaMemcpyDeviceToHost, st));
+    INFFT_TRY(read_back(&b2, bn, 8, st));
     INFFT_CUDA(cudaStreamSynchronize(st));
     const double bnorm = std::sqrt(b2);
 
@@ -390,7 +391,7 @@ static infft_status weights_impl(infft_plan_s* p, int max_iter, double rel_tol, 
         INFFT_LAUNCHED();
         INFFT_TRY(dot(r, r, n, part, sc + 4, st));
         double rr_new = 0;
-        INFFT_CUDA(cudaMemcpyAsync(&rr_new, sc + 4, 8, cudaMemcpyDeviceToHost, st));
+        INFFT_TRY(read_back(&rr_new, sc + 4, 8, st));
         k_cg_beta<<<1, 1, 0, st>>>(sc);
         INFFT_LAUNCHED();
         k_cg_update_p<<<eb, et, 0, st>>>(pv, r, n, sc);
@@ -427,7 +428,7 @@ static infft_status weights_impl(infft_plan_s* p, int max_iter, double rel_tol, 
         INFFT_LAUNCHED();
         k_max_final<<<1, RED_THREADS, 0, st>>>(part, sc + 8);
         INFFT_LAUNCHED();
-        INFFT_CUDA(cudaMemcpyAsync(residual_inf, sc + 8, 8, cudaMemcpyDeviceToHost, st));
+        INFFT_TRY(read_back(residual_inf, sc + 8, 8, st));
     }
     INFFT_CUDA(cudaStreamSynchronize(st));
     if (iters_out) *iters_out = it;
@@ -453,11 +454,13 @@ infft_status infft_weights_opts(infft_plan_t p, int max_iter, double rel_tol, in
         return INFFT_EINVAL;
     }
     std::vector<void*> tmp;
-    infft_plan_t sub = nullptr;
+    infft_plan_s* sub = nullptr;
+    p->pool_stream = (cudaStream_t)stream;
     infft_status s = weights_impl(p, max_iter, rel_tol, m_cg, opts, residual_inf, iters, (cudaStream_t)stream, tmp, sub);
+    // temporaries and the degree-2M plan go back to the pool in stream order
+    for (void* q : tmp) pool_free(q, (cudaStream_t)stream);
+    if (sub) plan_release(sub);
     cudaStreamSynchronize((cudaStream_t)stream);
-    for (void* q : tmp) cudaFree(q);
-    if (sub) infft_destroy(sub);
     return s;
 }
 
@@ -469,6 +472,7 @@ infft_status infft_weights(infft_plan_t p, int max_iter, double rel_tol, int m_c
 infft_status infft_set_weights(infft_plan_t p, const void* w, void* stream) {
     if (!p || !w) { set_error("null argument"); return INFFT_EINVAL; }
     cudaStream_t st = (cudaStream_t)stream;
+    p->pool_stream = st;
     INFFT_TRY(ensure_weight_buffers(p));
     const bool dev = is_device_pointer(w);
     INFFT_CUDA(cudaMemcpyAsync(p->w_master, w, (size_t)p->N * 16, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));

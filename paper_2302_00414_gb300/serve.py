@@ -16,8 +16,9 @@ device schedules their blocks ahead of the precompute's.  Every iteration of ``s
   admission); plans being built hold their estimate meanwhile.
 
 Transforms of one plan that overlap in time need separate scratch grids: every request
-in flight is given its own scratch set of the plan (``infft_adjoint_batched_slots``), so
-one point set can be in several running batches and repeat within a batch.
+in flight is given its own scratch set of the plan (``infft_adjoint_batched_slots``), the
+lowest one free, so one point set can be in several running batches and repeat within a
+batch.
 
 The compute happens in the CUDA library; this module only schedules calls.  The backend
 is injectable so that the scheduling logic can be tested without a GPU.
@@ -64,12 +65,24 @@ class Backend:
         import paper_2302_00414_gb300 as L
         self.torch, self.L = torch, L
         self.weights_iters, self.m, self.sigma = weights_iters, m, sigma
+        self._free, self._free_at = 0, -1.0
+        self.phase_s = collections.Counter()     # host seconds per build phase
+        self.launch_max = collections.Counter()  # longest host time of each launch phase
+        self.launch_sum = collections.Counter()
         L.load()
 
     def build_plan(self, ps: PointSet, stream):
+        t0 = time.perf_counter()
         x = ps.x() if callable(ps.x) else ps.x
-        p = self.L.Plan(x, ps.M, self.sigma, self.m, ps.precision, stream=stream.cuda_stream)
+        t1 = time.perf_counter()
+        # pooled plan memory: building and destroying plans does not stall the launches
+        p = self.L.Plan(x, ps.M, self.sigma, self.m, ps.precision, stream=stream.cuda_stream, pooled=True)
+        t2 = time.perf_counter()
         p.weights(max_iter=self.weights_iters, rel_tol=1e-12, stream=stream.cuda_stream)
+        t3 = time.perf_counter()
+        self.phase_s["points"] += t1 - t0
+        self.phase_s["plan"] += t2 - t1
+        self.phase_s["weights"] += t3 - t2
         return p
 
     def plan_bytes(self, plan) -> int:
@@ -82,7 +95,13 @@ class Backend:
         return 120 * n + 40 * grid + cg
 
     def free_bytes(self) -> int:
-        return int(self.torch.cuda.mem_get_info()[0])
+        # the device query can wait behind another thread's synchronising call (a plan's
+        # destruction, the precompute's frees): refresh it at most every 0.5 s
+        now = time.perf_counter()
+        if now - self._free_at > 0.5:
+            self._free = int(self.torch.cuda.mem_get_info()[0])
+            self._free_at = now
+        return self._free
 
     def new_stream(self, priority: int = 0):
         # lower number = higher priority: the device scheduler then prefers blocks of the
@@ -91,14 +110,21 @@ class Backend:
 
     def launch(self, plans, fs, stream, slots):
         torch = self.torch
+        t0 = time.perf_counter()
         with torch.cuda.stream(stream):
             # outputs allocated on the launch stream; inputs marked as used by it
             outs = [torch.empty((p.M,) * p.d, dtype=f.dtype, device=f.device) for p, f in zip(plans, fs)]
             for f in fs:
                 f.record_stream(stream)
+            t1 = time.perf_counter()
             self.L.adjoint_batched(plans, fs, outs, self.L.MODE_DCF, stream=stream.cuda_stream, slots=slots)
+            t2 = time.perf_counter()
             ev = torch.cuda.Event()
             ev.record(stream)
+        t3 = time.perf_counter()
+        for k, dt in (("alloc", t1 - t0), ("library", t2 - t1), ("event", t3 - t2)):
+            self.launch_max[k] = max(self.launch_max[k], dt)
+            self.launch_sum[k] += dt
         return outs, ev
 
     def done(self, ev) -> bool:
@@ -110,8 +136,12 @@ class Backend:
 
 class Server:
     def __init__(self, backend, mem_budget: Optional[int] = None, max_batch: int = 64, streams: int = 3,
-                 max_repeat: int = 8, clock: Callable[[], float] = time.perf_counter):
+                 max_repeat: int = 8, clock: Callable[[], float] = time.perf_counter,
+                 keep_output: Optional[Callable[[Request], bool]] = None):
         self.be = backend
+        # which completed requests keep their result tensor (all by default); dropping the
+        # others lets the allocator reuse their memory instead of growing the heap
+        self.keep_output = keep_output
         self.max_batch = max_batch
         self.max_repeat = max_repeat
         self.mem_budget = mem_budget
@@ -136,12 +166,19 @@ class Server:
         self._retry: collections.deque = collections.deque()   # sets waiting for memory, FIFO
         self._deferred_keys: set = set()
         self.build_times: List[tuple] = []    # (key, seconds) of every plan built
+        self.launch_times: List[float] = []   # host seconds of every batch launch
         self._lock = threading.Lock()
         self._work: queue.Queue = queue.Queue()
         self._ready: queue.Queue = queue.Queue()
         self._pstream = backend.new_stream(priority=0)
+        self._slots_busy: Dict[Any, set] = collections.defaultdict(set)   # scratch sets in flight
         self._worker = threading.Thread(target=self._precompute_loop, daemon=True)
         self._worker.start()
+        # evicted plans are destroyed off the scheduling thread: destroying a plan waits for
+        # the device, which would stall every reconstruction behind the precompute's kernels
+        self._released: queue.Queue = queue.Queue()
+        self._releaser = threading.Thread(target=self._release_loop, daemon=True)
+        self._releaser.start()
 
     # ---- admission of point sets ------------------------------------------------------
     def register(self, ps: PointSet, pin: bool = False):
@@ -162,6 +199,13 @@ class Server:
             except Exception as e:  # surfaced to the requests of this key
                 self._ready.put((ps.key, None, e))
 
+    def _release_loop(self):
+        while True:
+            plan = self._released.get()
+            if plan is None:
+                return
+            self.be.release(plan)
+
     def _make_room(self, need: int) -> bool:
         """Evict LRU plans that are not in flight until `need` more bytes fit."""
         def fits():
@@ -176,7 +220,7 @@ class Server:
             victim = min(idle, key=lambda k: self.plan_used[k])
             plan = self.plans.pop(victim)
             self.resident_bytes -= self.plan_size.pop(victim)
-            self.be.release(plan)
+            self._released.put(plan)
             self.stats["evicted"] += 1
         return True
 
@@ -219,18 +263,22 @@ class Server:
         """Retire finished batches, absorb new plans, launch ready requests; returns the
         number of requests still queued or in flight."""
         now = self.clock
+        t_step = time.perf_counter()
+        self.stats["steps"] += 1
         # finished batches
         still = []
-        for ev, reqs, sidx, outs in self.inflight:
+        for ev, reqs, sidx, outs, slots in self.inflight:
             if self.be.done(ev):
                 t = now()
-                for r, o in zip(reqs, outs):
-                    r.t_done, r.out = t, o
+                for r, o, sl in zip(reqs, outs, slots):
+                    r.t_done = t
+                    r.out = o if self.keep_output is None or self.keep_output(r) else None
                     self.plan_refs[r.key] -= 1
+                    self._slots_busy[r.key].discard(sl)
                     self.completed.append(r)
                 self.free_streams.append(sidx)
             else:
-                still.append((ev, reqs, sidx, outs))
+                still.append((ev, reqs, sidx, outs, slots))
         self.inflight = still
         # plans built by the worker
         while True:
@@ -249,11 +297,13 @@ class Server:
             self._n_parked -= len(waiting)
             self.plan_refs[key] += len(waiting)
             self.pending.extend(waiting)
+        t0 = time.perf_counter()
         while self._retry and self._admit(self._retry[0]):
             self._retry.popleft()
-        # launch: one batch per (d, precision) group into free stream slots.  The j-th
-        # request for a point set in the batch on stream s uses the plan's scratch set
-        # s * max_repeat + j, so batches on different streams never share scratch.
+        self.stats["admission_s"] += time.perf_counter() - t0
+        # launch: one batch per (d, precision) group into free stream slots.  Every request
+        # takes the lowest scratch set of its plan that no running request uses, so
+        # overlapping transforms never share scratch and most plans need only set 0.
         while self.pending and self.free_streams:
             groups: Dict[tuple, List[Request]] = collections.OrderedDict()
             per_key: Dict[Any, int] = collections.Counter()
@@ -282,21 +332,29 @@ class Server:
                     r.t_admit = t
                     r.batch_size = len(reqs)
                     self.plan_used[r.key] = t
-                occ: Dict[Any, int] = collections.Counter()
                 slots = []
                 for r in reqs:
-                    slots.append(sidx * self.max_repeat + occ[r.key])
-                    occ[r.key] += 1
+                    busy = self._slots_busy[r.key]
+                    sl = 0
+                    while sl in busy:
+                        sl += 1
+                    busy.add(sl)
+                    slots.append(sl)
+                t0 = time.perf_counter()
                 outs, ev = self.be.launch(plans, [r.f for r in reqs], self.streams[sidx], slots)
+                dt = time.perf_counter() - t0
+                self.stats["launch_s"] += dt
+                self.launch_times.append(dt)
                 for k in {r.key for r in reqs}:   # repeats may have grown the plan's scratch
                     b = self.be.plan_bytes(self.plans[k])
                     self.resident_bytes += b - self.plan_size.get(k, b)
                     self.plan_size[k] = b
-                self.inflight.append((ev, reqs, sidx, outs))
+                self.inflight.append((ev, reqs, sidx, outs, slots))
                 self.stats["batches"] += 1
                 self.stats["max_inflight"] = max(self.stats["max_inflight"], len(self.inflight))
+        self.stats["step_s"] += time.perf_counter() - t_step
         return len(self.pending) + self._n_parked + \
-            sum(len(r) for _, r, _, _ in self.inflight)
+            sum(len(r) for _, r, _, _, _ in self.inflight)
 
     def drain(self, timeout: float = 600.0):
         t0 = time.perf_counter()
@@ -308,6 +366,8 @@ class Server:
     def close(self):
         self._work.put(None)
         self._worker.join(timeout=5)
+        self._released.put(None)
+        self._releaser.join(timeout=5)
 
     def abort(self, timeout: float = 60.0):
         """Drop queued plan builds, wait for the one in progress and stop the worker."""
@@ -318,6 +378,8 @@ class Server:
                 break
         self._work.put(None)
         self._worker.join(timeout=timeout)
+        self._released.put(None)
+        self._releaser.join(timeout=timeout)
 
 
 def run_poisson(server: Server, requests: List[Request], rate: float, seed: int = 0,
@@ -357,6 +419,9 @@ def latency_summary(reqs: List[Request]) -> dict:
     def pct(q):
         return lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
     span = max(r.t_done for r in reqs) - min(r.t_arrive for r in reqs)
+    wait = sorted((r.t_admit - r.t_arrive) * 1e3 for r in reqs)
+    run = sorted((r.t_done - r.t_admit) * 1e3 for r in reqs)
     return {"requests": len(lat), "p50_ms": pct(0.50), "p99_ms": pct(0.99), "max_ms": lat[-1],
             "throughput_per_s": len(lat) / span if span > 0 else None,
-            "mean_batch": sum(r.batch_size for r in reqs) / len(reqs)}
+            "mean_batch": sum(r.batch_size for r in reqs) / len(reqs),
+            "queue_p50_ms": wait[len(wait) // 2], "launch_to_done_p50_ms": run[len(run) // 2]}
