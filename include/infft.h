@@ -218,7 +218,10 @@ infft_status infft_inverse_adjoint(infft_plan_t plan, const void* h, void* f, vo
  * with device buffers (several sample vectors on one point set, e.g. one per
  * receive coil): its k-th occurrence uses the k-th set of scratch grids, allocated
  * on first need and owned by the plan until infft_destroy (counted in
- * infft_plan_device_bytes).  The fhat[i] must not overlap.
+ * infft_plan_device_bytes).  The fhat[i] must not overlap.  The jobs run in three
+ * concurrent branches of unequal work on streams the library forks from `stream` (at its
+ * priority) and joins back to it; INFFT_BATCH_BRANCHES in the environment (1..8) changes
+ * the count.  Results do not depend on the branching.
  */
 infft_status infft_adjoint_batched(const infft_plan_t* plans, int count, int mode,
                                    const void* const* f, void* const* fhat, void* stream);
@@ -253,8 +256,9 @@ infft_status infft_adjoint_batched_timed(const infft_plan_t* plans, int count, i
  * Graph-replayed batches.  infft_batch_create records the batched adjoint for
  * fixed plans and fixed device buffers f[i] / fhat[i] into a CUDA graph;
  * infft_batch_run replays it on `stream`.  The plans and buffers must outlive
- * the batch.  Plans may repeat as in infft_adjoint_batched; the extra scratch
- * grids are allocated before the capture starts.
+ * the batch, and the buffers must be device memory.  The graph holds the jobs in the
+ * concurrent branches of infft_adjoint_batched.  Plans may repeat as in
+ * infft_adjoint_batched; the extra scratch grids are allocated before the capture starts.
  */
 infft_status infft_batch_create(const infft_plan_t* plans, int count, int mode,
                                 const void* const* f, void* const* fhat, void* stream,
