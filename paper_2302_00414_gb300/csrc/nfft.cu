@@ -280,6 +280,9 @@ __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> j
     const long long q0 = (long long)lb * L;
     const bool lanes_b = (B >= L);  // consecutive lines are consecutive b: coalesce along b
 
+    cx<R>* tws = buf + L * ns;      // the n/2 twiddles after the lines
+    for (int k = threadIdx.x; k < (Ms >> 1); k += blockDim.x) tws[k] = J.tw[k];
+
     const cx<R>* src;
     cx<R>* dst;
     if (!FWD) {
@@ -321,21 +324,51 @@ __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> j
     }
     __syncthreads();
 
+    // Butterflies in place, two radix-2 stages at a time: one thread takes the four
+    // elements j + k q (k = 0..3) of a group of 4q and applies the stage of half-length q
+    // (twiddle W_2q^pos) and then that of half-length 2q (W_4q^pos, W_4q^(pos+q)) in
+    // registers.  An odd number of stages starts with one radix-2 stage of half-length 1.
+    // Twiddles W_n^k = exp(-2 pi i k / n), k < n/2, come from shared memory (conjugated
+    // for the inverse direction).
     const int half_n = n >> 1;
     const int loghn = logn - 1;
-    for (int lh = 0; lh < logn; ++lh) {   // butterflies of half-length 2^lh
-        const int half = 1 << lh;
+    int lh = 0;
+    if (logn & 1) {
         for (int e = tid; e < L * half_n; e += nth) {
             const int l = e >> loghn, jj = e & (half_n - 1);
-            const int grp = jj >> lh, pos = jj & (half - 1);
-            const int i1 = grp * (half << 1) + pos, i2 = i1 + half;
-            cx<R> w = J.tw[pos << (loghn - lh)];
-            if (FWD) w.im = -w.im;
             cx<R>* row = buf + l * ns;
-            const cx<R> a = row[skew(i1)];
-            const cx<R> b = mul(w, row[skew(i2)]);
-            row[skew(i1)] = add(a, b);
-            row[skew(i2)] = sub(a, b);
+            const cx<R> a = row[skew(2 * jj)], b = row[skew(2 * jj + 1)];
+            row[skew(2 * jj)] = add(a, b);
+            row[skew(2 * jj + 1)] = sub(a, b);
+        }
+        __syncthreads();
+        lh = 1;
+    }
+    const int quarter_n = n >> 2;
+    const int logqn = logn - 2;
+    for (; lh < logn; lh += 2) {
+        const int q = 1 << lh;
+        for (int e = tid; e < L * quarter_n; e += nth) {
+            const int l = e >> logqn, jj = e & (quarter_n - 1);
+            const int grp = jj >> lh, pos = jj & (q - 1);
+            const int base = grp * (q << 2) + pos;
+            cx<R>* row = buf + l * ns;
+            const cx<R> a0 = row[skew(base)], a1 = row[skew(base + q)];
+            const cx<R> a2 = row[skew(base + 2 * q)], a3 = row[skew(base + 3 * q)];
+            cx<R> w1 = tws[pos << (logn - 1 - lh)];
+            cx<R> w2 = tws[pos << (logn - 2 - lh)];
+            cx<R> w3 = tws[(pos + q) << (logn - 2 - lh)];
+            if (FWD) { w1.im = -w1.im; w2.im = -w2.im; w3.im = -w3.im; }
+            cx<R> t = mul(w1, a1);
+            const cx<R> b0 = add(a0, t), b1 = sub(a0, t);
+            t = mul(w1, a3);
+            const cx<R> b2 = add(a2, t), b3 = sub(a2, t);
+            t = mul(w2, b2);
+            row[skew(base)] = add(b0, t);
+            row[skew(base + 2 * q)] = sub(b0, t);
+            t = mul(w3, b3);
+            row[skew(base + q)] = add(b1, t);
+            row[skew(base + 3 * q)] = sub(b1, t);
         }
         __syncthreads();
     }
@@ -504,7 +537,7 @@ template <class R, int D>
 static infft_status launch_fft_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* ev) {
     int maxMs = 0;
     for (int j = 0; j < js.njobs; ++j) maxMs = std::max(maxMs, js.job[j].Ms);
-    const size_t fsmem = (size_t)js.L * (maxMs + maxMs / 16) * sizeof(cx<R>);
+    const size_t fsmem = ((size_t)js.L * (maxMs + maxMs / 16) + maxMs / 2) * sizeof(cx<R>);
     INFFT_CUDA(cudaFuncSetAttribute(k_fft<R, D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
     for (int p = 0; p < D; ++p) {
         k_fft<R, D, false><<<js.pre_fft[p][js.njobs], 256, fsmem, st>>>(js, p);
@@ -570,7 +603,7 @@ static infft_status launch_forward(JobSet<R>& js, cudaStream_t st) {
     fill_prefixes(js, D, true);
     int maxMs = 0;
     for (int j = 0; j < js.njobs; ++j) maxMs = std::max(maxMs, js.job[j].Ms);
-    const size_t fsmem = (size_t)js.L * (maxMs + maxMs / 16) * sizeof(cx<R>);
+    const size_t fsmem = ((size_t)js.L * (maxMs + maxMs / 16) + maxMs / 2) * sizeof(cx<R>);
     INFFT_CUDA(cudaFuncSetAttribute(k_fft<R, D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
     for (int p = 0; p < D; ++p) {
         k_fft<R, D, true><<<js.pre_fft[p][js.njobs], 256, fsmem, st>>>(js, p);
@@ -635,7 +668,7 @@ template <class R, int D>
 static infft_status fft_passes_d(JobSet<R>& js, cudaStream_t st, bool forward) {
     fill_prefixes(js, D, forward);
     const int n = js.job[0].Ms;
-    const size_t fsmem = (size_t)js.L * (n + n / 16) * sizeof(cx<R>);
+    const size_t fsmem = ((size_t)js.L * (n + n / 16) + n / 2) * sizeof(cx<R>);
     if (forward) {
         INFFT_CUDA(cudaFuncSetAttribute(k_fft<R, D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
         for (int p = 0; p < D; ++p) {
