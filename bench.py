@@ -54,9 +54,11 @@ def parse():
     ap.add_argument("--cg-iters", type=int, default=25)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="C3", choices=["C1", "C2", "C3", "C4", "C5"],
+    ap.add_argument("--t51-max", type=int, default=1024, help="T51: largest M of the linogram sweep")
+    ap.add_argument("--t51-bopt-max", type=int, default=32, help="T51: largest M with B_opt (Algorithm 4.3)")
+    ap.add_argument("--config", default="C3", choices=["C1", "C2", "C3", "C4", "C5", "T51"],
                     help="C3 (default): the batched d=2 workload; C1/C2/C4: single-set workloads; "
-                         "C5: Poisson-arrival serving")
+                         "C5: Poisson-arrival serving; T51: the linogram sweep in the shape of Table 5.1")
     ap.add_argument("--rate", type=float, default=500.0, help="C5: mean arrival rate (requests/s)")
     ap.add_argument("--requests", type=int, default=20000, help="C5: number of requests")
     ap.add_argument("--new-frac", type=float, default=0.2, help="C5: fraction of requests on new point sets")
@@ -727,6 +729,116 @@ def run_serving(args, rank, world, dist):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------------------
+# linogram sweep in the shape of Table 5.1 (random coefficients in place of the phantom)
+
+def _timed_recon(L, torch, p, f, h, mode, steps):
+    b = L.Batch([p], [f], [h], mode)
+    for _ in range(3):
+        b.run()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        b.run()
+    e1.record(st)
+    torch.cuda.synchronize()
+    b.close()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_table51(args, rank, world, dist):
+    """M = 2^c, linogram grid R = 2M, T = 2R (N = 8 M^2 > |I_2M|), f = A fhat for random fhat:
+    relative error e_2 = ||h - fhat|| / ||fhat|| (eq. relative_errors), precompute and
+    reconstruction times of Algorithm 3.7 (weights of Algorithm 3.6, here FP64 with m = 8,
+    sigma = 2, and the FP32 fast path with m = 4) and of Algorithm 4.4 (B_opt of Algorithm 4.3,
+    FP64, sigma = 1, m = 4 as the paper states, with the Dirichlet window, the optimal one of
+    Theorem 4.5; the Kaiser-Bessel window gave e_2 = 1.5e-4 at M = 16).  From M = 64 on, the
+    columns at the grid's centre (all radii meet there) exceed what one column solve holds in
+    shared memory, so B_opt stops at --t51-bopt-max."""
+    import torch
+
+    import inputs
+    import paper_2302_00414_gb300 as L
+    from oracle import fourier as FO
+    from paper_2302_00414_gb300 import build as B
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    if dist is not None:
+        dist.barrier()
+    L.load()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    rows = []
+    M = 16
+    t_all = time.perf_counter()
+    while M <= args.t51_max:
+        x = inputs.linogram(2 * M, 4 * M)
+        N = x.shape[0]
+        fh = inputs.coeffs_complex((M, M), 5100 + M)
+        if N * M * M <= 2e9:   # the oracle's exact sums
+            f = FO.ndft(x, fh, M)
+            f_src = "exact sums (oracle)"
+        else:                   # as the paper: an NFFT of fhat (the library's FP64 NFFT, m = 10)
+            q = L.Plan(x, M, 2.0, 10, "fp64")
+            f = q.forward(torch.from_numpy(fh).to(dev)).cpu().numpy()
+            q.close()
+            f_src = "FP64 NFFT, m=10"
+        row = {"M": M, "N": int(N), "f": f_src}
+        fd = torch.from_numpy(f).to(dev)
+        # Algorithm 3.7, FP64
+        p = L.Plan(x, M, 2.0, 8, "fp64")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = p.weights(max_iter=500, rel_tol=1e-14)
+        row["dcf_fp64_precompute_s"] = time.perf_counter() - t0
+        row["dcf_fp64_cg_iters"] = info["iters"]
+        row["dcf_weight_residual"] = info["residual_inf"]
+        h = torch.empty((M, M), dtype=torch.complex128, device=dev)
+        row["dcf_fp64_recon_ms"] = _timed_recon(L, torch, p, fd, h, L.MODE_DCF, 10)
+        row["dcf_fp64_e2"] = float(np.linalg.norm(h.cpu().numpy() - fh) / np.linalg.norm(fh))
+        w = p.get_weights()
+        p.close()
+        # Algorithm 3.7, FP32 fast path with the same weights
+        p = L.Plan(x, M, 2.0, 4, "fp32")
+        p.set_weights(w)
+        f32 = fd.to(torch.complex64)
+        h32 = torch.empty((M, M), dtype=torch.complex64, device=dev)
+        row["dcf_fp32_recon_ms"] = _timed_recon(L, torch, p, f32, h32, L.MODE_DCF, 20)
+        row["dcf_fp32_e2"] = float(np.linalg.norm(h32.cpu().numpy() - fh) / np.linalg.norm(fh))
+        p.close()
+        # Algorithm 4.4
+        if M <= args.t51_bopt_max:
+            p = L.Plan(x, M, 1.0, 4, "fp64", window="dirichlet")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p.optimize_B()
+            row["bopt_precompute_s"] = time.perf_counter() - t0
+            hb = torch.empty((M, M), dtype=torch.complex128, device=dev)
+            row["bopt_recon_ms"] = _timed_recon(L, torch, p, fd, hb, L.MODE_BOPT, 10)
+            row["bopt_e2"] = float(np.linalg.norm(hb.cpu().numpy() - fh) / np.linalg.norm(fh))
+            p.close()
+        rows.append(row)
+        print(json.dumps({"t51_row": row}), file=sys.stderr, flush=True)
+        M *= 2
+    if rank != 0:
+        return
+    head = rows[-1]
+    line = {
+        "metric": "iNFFT recon time and e_2 on linogram grids (Table 5.1 shapes)",
+        "value": 1e3 / head["dcf_fp32_recon_ms"], "unit": "recon/s", "n_gpus": world, "steps": 10,
+        "warmup": 3, "ms_per_step": head["dcf_fp32_recon_ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "linogram R=2M, T=2R, N=8M^2, random fhat in place of the phantom; "
+                               "value: FP32 DCF reconstruction at the largest M", "name": "T51",
+                   "M": [r["M"] for r in rows]},
+        "rows": rows, "wall_s": time.perf_counter() - t_all,
+        "roofline": None, "e2e": None, "gpu_launches": None, "clocks": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -745,6 +857,8 @@ def main():
             run_single(args, rank, world, dist)
         elif args.config == "C5":
             run_serving(args, rank, world, dist)
+        elif args.config == "T51":
+            run_table51(args, rank, world, dist)
         else:
             run_ours(args, rank, world, dist)
     finally:
