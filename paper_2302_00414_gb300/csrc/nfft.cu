@@ -112,8 +112,9 @@ __device__ __forceinline__ cx<R> merged_cell(const Job<R>& J, long long cidx);
 // ---------------------------------------------------------------------------------------
 // Two-dimensional merge, one block per tile of T x T cells (T <= 16, T > m, Ms a multiple
 // of T), one thread per cell.  Along an axis, the cell at offset r in tile t lies in the
-// padded tile of t at r + m, of t - 1 at r + T + m when r <= m, and of t + 1 at
-// r - T + m when r >= T - m (tile indices mod ntile): at most two sources per axis.
+// padded tile of t at r + m, of t - 1 at r + T + m when that is < P, and of t + 1 at
+// r - T + m when that is >= 0 (tile indices mod ntile): with 2m < T at most two sources
+// per axis.
 template <class R>
 __global__ void __launch_bounds__(256) k_merge2d(const __grid_constant__ JobSet<R> js) {
     const int gblk = blockIdx.x;
@@ -128,10 +129,10 @@ __global__ void __launch_bounds__(256) k_merge2d(const __grid_constant__ JobSet<
     int ny = 1, nx = 1;
     yt[0] = ty; yo[0] = r + m;
     xt[0] = tx; xo[0] = c + m;
-    if (r <= m) { yt[1] = (ty - 1 + nt) % nt; yo[1] = r + T + m; ny = 2; }
-    else if (r >= T - m) { yt[1] = (ty + 1) % nt; yo[1] = r - T + m; ny = 2; }
-    if (c <= m) { xt[1] = (tx - 1 + nt) % nt; xo[1] = c + T + m; nx = 2; }
-    else if (c >= T - m) { xt[1] = (tx + 1) % nt; xo[1] = c - T + m; nx = 2; }
+    if (r + T + m < P) { yt[1] = (ty - 1 + nt) % nt; yo[1] = r + T + m; ny = 2; }
+    else if (r - T + m >= 0) { yt[1] = (ty + 1) % nt; yo[1] = r - T + m; ny = 2; }
+    if (c + T + m < P) { xt[1] = (tx - 1 + nt) % nt; xo[1] = c + T + m; nx = 2; }
+    else if (c - T + m >= 0) { xt[1] = (tx + 1) % nt; xo[1] = c - T + m; nx = 2; }
     const size_t cells = (size_t)P * P;
     cx<R> acc = mk<R>(0, 0);
     for (int a = 0; a < ny; ++a) {
@@ -148,8 +149,8 @@ __global__ void __launch_bounds__(256) k_merge2d(const __grid_constant__ JobSet<
 // ---------------------------------------------------------------------------------------
 // Three-dimensional merge, one block per tile of T^3 cells (T a power of two, m < T),
 // threads striding over the tile's cells.  Along an axis the cell at offset r of tile t
-// lies in the padded tile of t at r + m, of t - 1 at r + T + m when r <= m, and of t + 1
-// at r - T + m when r >= T - m; with T <= 2m both neighbours can hold it.  Work items of
+// lies in the padded tile of t at r + m, of t - 1 at r + T + m when that is < P, and of
+// t + 1 at r - T + m when that is >= 0; with T <= 2m both neighbours can hold it.  Work items of
 // a source tile are summed in item order, sources in a fixed order: deterministic.
 template <class R>
 __global__ void __launch_bounds__(256) k_merge3d(const __grid_constant__ JobSet<R> js) {
@@ -169,8 +170,8 @@ __global__ void __launch_bounds__(256) k_merge3d(const __grid_constant__ JobSet<
         for (int a = 0; a < 3; ++a) {
             const int r = rr[a], t = tt[a];
             st[a][0] = t; so[a][0] = r + m; ns[a] = 1;
-            if (r <= m) { st[a][ns[a]] = (t - 1 + nt) % nt; so[a][ns[a]] = r + T + m; ++ns[a]; }
-            if (r >= T - m) { st[a][ns[a]] = (t + 1) % nt; so[a][ns[a]] = r - T + m; ++ns[a]; }
+            if (r + T + m < P) { st[a][ns[a]] = (t - 1 + nt) % nt; so[a][ns[a]] = r + T + m; ++ns[a]; }
+            if (r - T + m >= 0) { st[a][ns[a]] = (t + 1) % nt; so[a][ns[a]] = r - T + m; ++ns[a]; }
         }
         cx<R> acc = mk<R>(0, 0);
         for (int a = 0; a < ns[0]; ++a)

@@ -298,7 +298,10 @@ Job<R> make_job(const infft_plan_s* p, int mode, const void* in, void* out, int 
     Job<R> J;
     memset(&J, 0, sizeof(J));
     J.d = p->d; J.M = p->M; J.Ms = p->Ms; J.m = p->m;
-    J.N = (int)p->N; J.T = p->T; J.ntile = p->ntile; J.P = p->P;
+    J.N = (int)p->N; J.T = p->T; J.ntile = p->ntile;
+    // padded edge: the window's 2m+1 taps need T + 2m, the 2m+2 slots of B_opt T + 2m + 1
+    // (the plan's P, which sizes the scratch)
+    J.P = (mode == INFFT_MODE_BOPT) ? p->P : p->T + 2 * p->m;
     J.nitems = p->nitems; J.window = p->window; J.mode = mode; J.S = p->S;
     J.beta = (R)p->beta; J.inv_m = (R)(1.0 / p->m);
     J.perm = p->perm; J.cell = p->cell; J.u = (const R*)p->u;

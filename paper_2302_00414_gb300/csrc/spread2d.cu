@@ -183,7 +183,8 @@ static infft_status launch_spread2d(JobSet<R>& js, cudaStream_t st, int m) {
         case 4: return launch_spread2d_m<R, 4, BOPT>(js, st);
         case 5: return launch_spread2d_m<R, 5, BOPT>(js, st);
         case 6: return launch_spread2d_m<R, 6, BOPT>(js, st);
-        default: return launch_spread2d_m<R, 7, BOPT>(js, st);
+        case 7: return launch_spread2d_m<R, 7, BOPT>(js, st);
+        default: return launch_spread2d_m<R, 8, BOPT>(js, st);
     }
 }
 
@@ -196,7 +197,7 @@ static bool spread2d_eligible(const JobSet<R>& js, int* m_out, bool* bopt_out) {
         const Job<R>& J = js.job[j];
         if (J.d != 2 || J.m != m || (J.mode == INFFT_MODE_BOPT) != bopt || J.P > 32) return false;
     }
-    if (m < 2 || m > 7) return false;
+    if (m < 2 || m > 8) return false;   // m = 8 with window taps only: P = 16 + 16 <= 32
     *m_out = m;
     *bopt_out = bopt;
     return true;

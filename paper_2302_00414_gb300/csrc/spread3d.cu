@@ -8,7 +8,7 @@ namespace infft {
 
 // ---------------------------------------------------------------------------------------
 // Three-dimensional spreading (window modes), tiles of 8^3 cells.  One warp per work item,
-// the item's padded tile of P^3 cells (P = 8 + 2m + 1) in shared memory.  Lane l takes
+// the item's padded tile of P^3 cells (P = 8 + 2m, the window's taps) in shared memory.  Lane l takes
 // the (z, x) tap pairs q = l + 32 r of a point (W^2 pairs, ceil(W^2 / 32) rounds) and
 // holds the W cells of each pair along y in registers, adding (c_j psi_y) psi_z psi_x.
 // The items' points are sorted by base cell: while consecutive points share their base
@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(64) k_spread3d(const __grid_constant__ JobSet<
     constexpr int WE = W + 1;                  // even stride of the staged rows
     constexpr int NR = (W * W + 31) / 32;      // rounds over the (z, x) pairs
     constexpr int T = SPREAD3D_T;
-    constexpr int P = T + 2 * MM + 1, P2 = P * P;
+    constexpr int P = T + 2 * MM, P2 = P * P;   // the padded edge of window modes
     constexpr int PZ = spread3d_plane(P, W), SC = P * PZ;
     constexpr bool F32 = sizeof(R) == 4;
     using V2 = typename std::conditional<F32, float2, double2>::type;
@@ -170,7 +170,7 @@ template <class R, int MM>
 static infft_status launch_spread3d_m(JobSet<R>& js, cudaStream_t st) {
     constexpr int W = 2 * MM + 1;
     constexpr int WE = W + 1;
-    constexpr int P = SPREAD3D_T + 2 * MM + 1;
+    constexpr int P = SPREAD3D_T + 2 * MM;
     const size_t cells = (size_t)P * spread3d_plane(P, W);
     size_t spw = ((cells + 1) & ~(size_t)1) * sizeof(cx<R>) + 32 * WE * (sizeof(cx<R>) + 2 * sizeof(R)) +
                  32 * sizeof(int) + (WPOLY_DEG + 1) * wpoly_stride(W) * sizeof(float);
