@@ -294,18 +294,30 @@ __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> j
         dst = (pass == D - 1) ? J.grid : (pass == 0 ? J.tmp1 : J.tmp2);
     }
     const int tid = threadIdx.x, nth = blockDim.x;
+    const int logL = 31 - __clz(L);   // L is a power of two
+
+    // offsets of each line's first element in the source and destination tensors (line l of
+    // the block is (a, b) = divmod(q0 + l, B); element i sits i * B further), or -1 past the end
+    __shared__ long long s_in[32], s_out[32];
+    if (tid < L) {
+        const long long q = q0 + tid;
+        long long bi = -1, bo = -1;
+        if (q < nlines) {
+            const long long a = q / B, b = q - a * B;
+            bi = (a * (FWD ? M : n)) * B + b;
+            bo = (a * (FWD ? n : M)) * B + b;
+        }
+        s_in[tid] = bi;
+        s_out[tid] = bo;
+    }
+    __syncthreads();
 
     if (!FWD) {
         for (int e = tid; e < L * n; e += nth) {
             int l, i;
-            if (lanes_b) { l = e % L; i = e / L; } else { i = e & (n - 1); l = e >> logn; }
-            const long long q = q0 + l;
-            cx<R> v = mk<R>(0, 0);
-            if (q < nlines) {
-                const long long a = q / B, b = q - a * B;
-                const long long g = (a * n + i) * B + b;
-                v = src[g];
-            }
+            if (lanes_b) { l = e & (L - 1); i = e >> logL; } else { i = e & (n - 1); l = e >> logn; }
+            const long long g0 = s_in[l];
+            const cx<R> v = (g0 >= 0) ? src[g0 + (long long)i * B] : mk<R>(0, 0);
             buf[l * ns + skew(bitrev(i, logn))] = v;
         }
     } else {
@@ -313,11 +325,10 @@ __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> j
         __syncthreads();
         for (int e = tid; e < L * M; e += nth) {
             int l, i;
-            if (lanes_b) { l = e % L; i = e / L; } else { i = e % M; l = e / M; }
-            const long long q = q0 + l;
-            if (q < nlines) {
-                const long long a = q / B, b = q - a * B;
-                const cx<R> v = scale(src[(a * M + i) * B + b], J.dinv[i]);
+            if (lanes_b) { l = e & (L - 1); i = e >> logL; } else { i = e % M; l = e / M; }
+            const long long g0 = s_in[l];
+            if (g0 >= 0) {
+                const cx<R> v = scale(src[g0 + (long long)i * B], J.dinv[i]);
                 const int bin = mod_pos(i - M / 2, Ms);
                 buf[l * ns + skew(bitrev(bin, logn))] = v;
             }
@@ -377,23 +388,19 @@ __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> j
     if (!FWD) {
         for (int e = tid; e < L * M; e += nth) {
             int l, i;
-            if (lanes_b) { l = e % L; i = e / L; } else { i = e % M; l = e / M; }
-            const long long q = q0 + l;
-            if (q < nlines) {
-                const long long a = q / B, b = q - a * B;
+            if (lanes_b) { l = e & (L - 1); i = e >> logL; } else { i = e % M; l = e / M; }
+            const long long g0 = s_out[l];
+            if (g0 >= 0) {
                 const int bin = mod_pos(i - M / 2, Ms);
-                dst[(a * M + i) * B + b] = scale(buf[l * ns + skew(bin)], J.dinv[i]);
+                dst[g0 + (long long)i * B] = scale(buf[l * ns + skew(bin)], J.dinv[i]);
             }
         }
     } else {
         for (int e = tid; e < L * n; e += nth) {
             int l, i;
-            if (lanes_b) { l = e % L; i = e / L; } else { i = e & (n - 1); l = e >> logn; }
-            const long long q = q0 + l;
-            if (q < nlines) {
-                const long long a = q / B, b = q - a * B;
-                dst[(a * n + i) * B + b] = buf[l * ns + skew(i)];
-            }
+            if (lanes_b) { l = e & (L - 1); i = e >> logL; } else { i = e & (n - 1); l = e >> logn; }
+            const long long g0 = s_out[l];
+            if (g0 >= 0) dst[g0 + (long long)i * B] = buf[l * ns + skew(i)];
         }
     }
 }
