@@ -34,8 +34,10 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
 
     unsigned char* base = smem_raw + (size_t)warp * js.smem_per_warp;
     cx<R>* cy = reinterpret_cast<cx<R>*>(base);            // [32][WE] c_j psi_y (window mode)
-    R* psx = reinterpret_cast<R*>(cy + 32 * WE);            // [32][WE] psi_x
-    int* meta = reinterpret_cast<int*>(psx + 32 * WE);      // [32][3]  oy, ox, sorted index
+    // psi_x of each staged point laid out by padded column, zero off the point's taps, so
+    // that lane l reads its column's weight directly (row pitch 33: conflict-free both ways)
+    R* psx = reinterpret_cast<R*>(cy + 32 * WE);            // [32][33] psi_x by column
+    int* meta = reinterpret_cast<int*>(psx + 32 * 33);      // [32][3]  oy, ox, sorted index
     cx<R>* cst = reinterpret_cast<cx<R>*>(meta + 96);       // [32]     c_j (B_opt mode)
     float* poly = reinterpret_cast<float*>(cst + 32);       // [(WPOLY_DEG+1) * WP] window polynomial (16-byte rows)
     const bool use_poly = F32 && !BOPT && J.wpoly != nullptr;
@@ -85,10 +87,14 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
                         wx[s] = tap_weight<R>(J.window, ux, s, MM, J.inv_m, J.beta);
                     }
                 }
+                R* row = psx + lane * 33;
+#pragma unroll
+                for (int c = 0; c < 32; ++c) row[c] = R(0);
+                const int oxl = cxl - tx * T;   // ox + s <= T - 1 + 2m = P - 1 < 32
 #pragma unroll
                 for (int s = 0; s < W; ++s) {
                     cy[lane * WE + s] = scale(fv, wy[s]);
-                    psx[lane * WE + s] = wx[s];
+                    row[oxl + s] = wx[s];
                 }
                 cy[lane * WE + W] = mk<R>(0, 0);
             }
@@ -105,9 +111,9 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
                 acc[WR - 1].y = R(0);
                 ++r0;
             }
-            const int sx = lane - ox;
             if (BOPT) {
                 constexpr int S = W + 1;
+                const int sx = lane - ox;
                 if (sx >= 0 && sx < S) {
                     const int i = meta[p * 3 + 2];
                     const cx<R> cv = cst[p];
@@ -120,8 +126,7 @@ __global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet
                     }
                 }
             } else {
-                const bool in = (sx >= 0) && (sx < W);
-                const R wx = in ? psx[p * WE + (in ? sx : 0)] : R(0);
+                const R wx = psx[p * 33 + lane];
                 const cx<R>* cp = cy + p * WE;
                 if constexpr (F32) {
                     // two complex coefficients per 16-byte broadcast load, one packed
@@ -161,7 +166,7 @@ template <class R, int MM, bool BOPT>
 static infft_status launch_spread2d_m(JobSet<R>& js, cudaStream_t st) {
     constexpr int W = 2 * MM + 1;
     constexpr int WE = W + 1;
-    size_t spw = 32 * WE * sizeof(cx<R>) + 32 * WE * sizeof(R) + 96 * sizeof(int) + 32 * sizeof(cx<R>) +
+    size_t spw = 32 * WE * sizeof(cx<R>) + 32 * 33 * sizeof(R) + 96 * sizeof(int) + 32 * sizeof(cx<R>) +
                  (WPOLY_DEG + 1) * wpoly_stride(W) * sizeof(float);
     spw = (spw + 15) & ~(size_t)15;
     js.smem_per_warp = (int)spw;
