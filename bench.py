@@ -111,6 +111,27 @@ def batch_rate_from_cost(cost, sets):
 
 
 # --------------------------------------------------------------------------------------
+# replicas on several ranks (one process per GPU, no data-path collective): the timed
+# region of every rank, the maximum over ranks, and the whole-job rate
+
+def reduce_over_ranks(x: float, dist, op: str = "max", device=None) -> float:
+    """x reduced over all ranks ("max" or "sum"); x itself on one rank."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank: float, ms_local: float, world: int, dist, device=None):
+    """Whole-job rate of weak-scaled replicas: all ranks' units over the slowest rank's time.
+    Returns (units per second, the slowest rank's milliseconds)."""
+    ms = reduce_over_ranks(ms_local, dist, "max", device)
+    return world * units_per_rank / (ms / 1e3), ms
+
+
+# --------------------------------------------------------------------------------------
 
 class ClockSampler:
     """nvidia-smi clock/throttle sampling during the timed region."""
@@ -299,11 +320,7 @@ def run_ours(args, rank, world, dist):
         dist.barrier()
     total_ms = e_all0.elapsed_time(e_all1)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    recon_per_s = world * len(plans) * args.steps / (total_ms / 1e3)
+    recon_per_s, total_ms = replica_rate(len(plans) * args.steps, total_ms, world, dist, dev)
 
     # ---- stage times (spread roofline) ---------------------------------------------------
     stage = []
@@ -480,11 +497,7 @@ def run_single(args, rank, world, dist):
                 ev[k][1].record(stream)
             e1.record(stream)
             torch.cuda.synchronize()
-        total_ms = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([total_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = reduce_over_ranks(e0.elapsed_time(e1), dist, "max", dev)
         step_ms = [a.elapsed_time(b) for a, b in ev]
         stage = [L.adjoint_batched_timed([p], [f], [h], L.MODE_DCF) for _ in range(5)]
         st = {"spread": statistics.median(s_["spread"] for s_ in stage),
@@ -692,11 +705,7 @@ def run_serving(args, rank, world, dist):
             ref = _oracle_parity((x, w * r.f.cpu().numpy().astype(np.complex128), M, ks))
             got = r.out.cpu().numpy().ravel()[ks]
             rel_errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
-    thr = len(done) / wall
-    if dist is not None:
-        t = torch.tensor([thr], device=dev)
-        dist.all_reduce(t)
-        thr = float(t.item())
+    thr = reduce_over_ranks(len(done) / wall, dist, "sum", dev)
     if rank != 0:
         return
     line = {

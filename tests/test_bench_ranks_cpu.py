@@ -1,0 +1,64 @@
+"""The multi-rank path of bench.py on the CPU: two gloo ranks run the replica aggregation
+(barrier, maximum of the timed region over ranks, whole-job rate) and the reference arm,
+which works on rank 0 only."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as tmp  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import bench
+        dist.barrier()
+        ms_local = 10.0 * (rank + 1)           # rank 1 is the slowest
+        rate, ms = bench.replica_rate(64 * 5, ms_local, world, dist, device="cpu")
+        total = bench.reduce_over_ranks(rank + 1.0, dist, "sum", device="cpu")
+        out[rank] = (rate, ms, total)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_replica_rate_takes_the_slowest_rank():
+    world, port = 2, _free_port()
+    out = tmp.Manager().dict()
+    tmp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
+    for rank in range(world):
+        rate, ms, total = out[rank]
+        assert ms == 20.0
+        assert rate == pytest.approx(world * 64 * 5 / 0.020)
+        assert total == 3.0
+
+
+def test_single_rank_needs_no_process_group():
+    import bench
+    rate, ms = bench.replica_rate(100, 50.0, 1, None)
+    assert (rate, ms) == (2000.0, 50.0)
+    assert bench.reduce_over_ranks(7.0, None) == 7.0
+
+
+def test_reference_arm_works_on_rank_0_only(capsys):
+    import sys
+
+    import bench
+    argv = sys.argv
+    sys.argv = ["bench.py", "--impl", "reference", "--gpus", "2"]
+    try:
+        args = bench.parse()
+    finally:
+        sys.argv = argv
+    assert bench.run_reference(args, rank=1, world=2) is None
+    assert capsys.readouterr().out == ""
