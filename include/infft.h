@@ -218,10 +218,11 @@ infft_status infft_inverse_adjoint(infft_plan_t plan, const void* h, void* f, vo
  * with device buffers (several sample vectors on one point set, e.g. one per
  * receive coil): its k-th occurrence uses the k-th set of scratch grids, allocated
  * on first need and owned by the plan until infft_destroy (counted in
- * infft_plan_device_bytes).  The fhat[i] must not overlap.  The jobs run in three
- * concurrent branches of unequal work on streams the library forks from `stream` (at its
- * priority) and joins back to it; INFFT_BATCH_BRANCHES in the environment (1..8) changes
- * the count.  Results do not depend on the branching.
+ * infft_plan_device_bytes).  The fhat[i] must not overlap.  The jobs run in three (six
+ * when host buffers are involved) concurrent branches of unequal work on streams the
+ * library forks from `stream` (at its priority) and joins back to it;
+ * INFFT_BATCH_BRANCHES in the environment (1..8) changes the count.  Results do not depend
+ * on the branching.
  */
 infft_status infft_adjoint_batched(const infft_plan_t* plans, int count, int mode,
                                    const void* const* f, void* const* fhat, void* stream);

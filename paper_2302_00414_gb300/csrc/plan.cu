@@ -726,10 +726,12 @@ static infft_status run_batched(const infft_plan_t* plans, int count, int mode, 
 // passes (and, with host buffers, the copies) of the smaller groups overlap the spreading
 // of the larger ones and the spreads fill each other's tails.  Measured on the batched
 // d = 2 workload (graph replay): 1, 2, 3, 4 branches give 71.3k, 76.5k, 77.3k, 76.9k
-// reconstructions/s; serialising the spreads across equal groups was slower.  The
-// environment variable INFFT_BATCH_BRANCHES (1..8) overrides G = 3.
-static int branch_count(int count) {
-    int G = 3;
+// reconstructions/s; serialising the spreads across equal groups was slower.  With host
+// buffers the copies gain from more branches (end to end 1 / 3 / 6 branches: 39.8k / 53.8k /
+// 57.4k reconstructions/s), so those calls take 6.  The environment variable
+// INFFT_BATCH_BRANCHES (1..8) overrides both.
+static int branch_count(int count, bool host_buffers = false) {
+    int G = host_buffers ? 6 : 3;
     if (const char* env = getenv("INFFT_BATCH_BRANCHES")) G = std::max(1, std::min(8, atoi(env)));
     return std::max(1, std::min(G, count));
 }
@@ -782,12 +784,15 @@ static infft_status run_branched(const infft_plan_t* plans, int count, int mode,
                                  void* const* fhat, cudaStream_t st, const int* slots_in) {
     std::vector<int> slot;
     INFFT_TRY(prepare_batched(plans, count, f, fhat, slots_in, slot, st));
-    const int G = branch_count(count);
+    bool host_out = false, host_in = false;
+    for (int i = 0; i < count; ++i) {
+        host_out = host_out || !is_device_pointer(fhat[i]);
+        host_in = host_in || !is_device_pointer(f[i]);
+    }
+    const int G = branch_count(count, host_in || host_out);
     if (G == 1) return run_batched(plans, count, mode, f, fhat, st, nullptr, slot.data());
     BranchSet* b = nullptr;
     INFFT_TRY(branch_set(st, &b));
-    bool host_out = false;
-    for (int i = 0; i < count; ++i) host_out = host_out || !is_device_pointer(fhat[i]);
     const std::vector<std::vector<int>> grp = split_groups(plans, count, G);
     INFFT_CUDA(cudaEventRecord(b->e[8], st));
     infft_status s = INFFT_OK;
