@@ -116,7 +116,7 @@ enum {
  * With INFFT_POOLED they come from a stream-ordered pool the library owns per device,
  * allocated in the order of the stream of the call that needs them (creation, later
  * batched calls, weights, B_opt) and returned in infft_destroy after a device
- * synchronisation; freed blocks stay in the pool for reuse until the process exits.
+ * synchronisation; the pool keeps up to 1 GiB of freed blocks for reuse.
  * Meant for servers that build plans on one thread while another launches
  * reconstructions.
  */

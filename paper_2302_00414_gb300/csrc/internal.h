@@ -77,8 +77,8 @@ struct infft_batch_s {
 
 namespace infft {
 
-// Stream-ordered device memory from a pool the library owns per device (its release
-// threshold is unlimited, so freed blocks are kept for reuse).  Neither call synchronises
+// Stream-ordered device memory from a pool the library owns per device (up to 1 GiB of
+// freed blocks is kept for reuse).  Neither call synchronises
 // the device, unlike cudaMalloc / cudaFree, so a thread building plans or weights does not
 // hold up other threads' launches.  Memory is usable in stream order on `st`.
 infft_status pool_alloc(void** ptr, size_t bytes, cudaStream_t st);

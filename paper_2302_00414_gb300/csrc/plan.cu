@@ -45,7 +45,9 @@ infft_status pool_alloc(void** ptr, size_t bytes, cudaStream_t st) {
             props.location.type = cudaMemLocationTypeDevice;
             props.location.id = dev;
             INFFT_CUDA(cudaMemPoolCreate(&g_pool[dev], &props));
-            uint64_t keep = UINT64_MAX;
+            // keep up to 1 GiB of freed blocks for reuse; the rest goes back to the device
+            // at the next synchronisation (a weights solve frees several GB of temporaries)
+            uint64_t keep = 1ull << 30;
             INFFT_CUDA(cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep));
         }
         pool = g_pool[dev];
