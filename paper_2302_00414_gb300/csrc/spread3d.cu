@@ -181,7 +181,7 @@ static infft_status launch_spread3d_m(JobSet<R>& js, cudaStream_t st) {
         return INFFT_EUNSUPPORTED;
     }
     js.smem_per_warp = (int)spw;
-    js.wpb = spw > 48 * 1024 ? 1 : 2;
+    js.wpb = 1;   // one warp per block packs the 34-40 KB tiles tightest: 5 warps per SM at m = 4
     const int nitems = js.pre_items[js.njobs];
     if (nitems == 0) return INFFT_OK;
     const size_t smem = spw * js.wpb;
