@@ -17,7 +17,10 @@ namespace infft {
 // cell is stored exactly once, no shared-memory read-modify-write, no atomics.
 // Window values are computed once per point while staging 32 points per warp.
 template <class R, int MM, bool BOPT>
-__global__ void __launch_bounds__(128) k_spread2d(const __grid_constant__ JobSet<R> js) {
+// float32 with m <= 4: at most 80 registers, so six 4-warp blocks (24 warps) share an SM
+// (batched d = 2, m = 4: spread 0.607 -> 0.574 ms); m = 5 would spill at that bound
+__global__ void __launch_bounds__(128, (sizeof(R) == 4 && MM <= 4 && !BOPT) ? 6 : 1)
+    k_spread2d(const __grid_constant__ JobSet<R> js) {
     constexpr int W = 2 * MM + 1;              // window taps per axis
     constexpr int WE = W + 1;                  // even stride of the staged rows (16-byte loads)
     constexpr int WR = BOPT ? W + 1 : W;       // rows held in registers
