@@ -218,7 +218,7 @@ infft_status infft_inverse_adjoint(infft_plan_t plan, const void* h, void* f, vo
  * with device buffers (several sample vectors on one point set, e.g. one per
  * receive coil): its k-th occurrence uses the k-th set of scratch grids, allocated
  * on first need and owned by the plan until infft_destroy (counted in
- * infft_plan_device_bytes).  The fhat[i] must not overlap.  The jobs run in three (six
+ * infft_plan_device_bytes).  The fhat[i] must not overlap.  The jobs run in three (eight
  * when host buffers are involved) concurrent branches of unequal work on streams the
  * library forks from `stream` (at its priority) and joins back to it;
  * INFFT_BATCH_BRANCHES in the environment (1..8) changes the count.  Results do not depend

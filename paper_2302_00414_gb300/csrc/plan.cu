@@ -729,11 +729,11 @@ static infft_status run_batched(const infft_plan_t* plans, int count, int mode, 
 // of the larger ones and the spreads fill each other's tails.  Measured on the batched
 // d = 2 workload (graph replay): 1, 2, 3, 4 branches give 71.3k, 76.5k, 77.3k, 76.9k
 // reconstructions/s; serialising the spreads across equal groups was slower.  With host
-// buffers the copies gain from more branches (end to end 1 / 3 / 6 branches: 39.8k / 53.8k /
-// 57.4k reconstructions/s), so those calls take 6.  The environment variable
-// INFFT_BATCH_BRANCHES (1..8) overrides both.
+// buffers the copies gain from more branches (end to end 1 / 3 / 6 / 8 branches: 39.8k /
+// 53.8k / 57.4k / 63.4k reconstructions/s before later kernel changes), so those calls take 8.
+// The environment variable INFFT_BATCH_BRANCHES (1..8) overrides both.
 static int branch_count(int count, bool host_buffers = false) {
-    int G = host_buffers ? 6 : 3;
+    int G = host_buffers ? 8 : 3;
     if (const char* env = getenv("INFFT_BATCH_BRANCHES")) G = std::max(1, std::min(8, atoi(env)));
     return std::max(1, std::min(G, count));
 }
