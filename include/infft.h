@@ -297,6 +297,17 @@ size_t infft_plan_device_bytes(infft_plan_t plan);   /* device memory held by th
 const char* infft_last_error(void);
 void infft_destroy(infft_plan_t plan);
 
+/*
+ * infft_inject_faults -- host-side fault injection for testing callers' error handling
+ * (no counterpart in the paper).  Bits: 1 every device allocation of a plan fails
+ * (INFFT_ENOMEM), 2 every kernel launch reports failure (INFFT_ECUDA; the kernel was
+ * still queued, nothing faults on the device), 4 the weights CG reports non-convergence
+ * (INFFT_ENOTCONV, weights stored).  0 turns injection off.  The initial mask comes from
+ * the environment variable INFFT_FAULT, a comma-separated list of alloc, launch, cg.
+ * Process-wide.
+ */
+void infft_inject_faults(unsigned mask);
+
 /* Number of kernel launches issued by this thread since the last reset
  * (for reporting; not synchronised with the device). */
 uint64_t infft_launch_count(void);

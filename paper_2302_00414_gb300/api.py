@@ -66,6 +66,7 @@ _SIGS = {
     "infft_last_error": (C.c_char_p, []),
     "infft_destroy": (None, [C.c_void_p]),
     "infft_launch_count": (C.c_uint64, []),
+    "infft_inject_faults": (None, [C.c_uint]),
     "infft_launch_count_reset": (None, []),
 }
 
@@ -99,6 +100,12 @@ def last_error() -> str:
 
 def launch_count() -> int:
     return int(load().infft_launch_count())
+
+
+def inject_faults(mask: int):
+    """Host-side fault injection: 1 allocations fail, 2 launches report failure, 4 CG does
+    not converge; 0 off."""
+    load().infft_inject_faults(int(mask))
 
 
 def launch_count_reset():

@@ -99,6 +99,10 @@ void plan_release(infft_plan_s* p);
 void set_error(const char* fmt, ...);
 void count_launch(int n = 1);
 
+// host-side fault injection (infft_inject_faults / INFFT_FAULT): true when `bit` is set
+enum { FAULT_ALLOC = 1, FAULT_LAUNCH = 2, FAULT_CG = 4 };
+bool fault(unsigned bit);
+
 #define INFFT_CUDA(call)                                                                   \
     do {                                                                                   \
         cudaError_t e__ = (call);                                                          \
@@ -112,6 +116,10 @@ void count_launch(int n = 1);
 #define INFFT_LAUNCHED()                                                                   \
     do {                                                                                   \
         infft::count_launch();                                                             \
+        if (infft::fault(infft::FAULT_LAUNCH)) {                                           \
+            infft::set_error("injected launch failure (%s:%d)", __FILE__, __LINE__);       \
+            return INFFT_ECUDA;                                                            \
+        }                                                                                  \
         cudaError_t e__ = cudaGetLastError();                                              \
         if (e__ != cudaSuccess) {                                                          \
             infft::set_error("kernel launch failed: %s (%s:%d)", cudaGetErrorString(e__),  \

@@ -1,6 +1,7 @@
 // Plan creation (point binning, tables) and the C-ABI entry points of the
 // transforms (Algorithms 2.1, 2.4, 3.7, 4.4).
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <mutex>
 #include <cmath>
@@ -26,6 +27,30 @@ void set_error(const char* fmt, ...) {
     va_end(ap);
 }
 void count_launch(int n) { g_launches += (uint64_t)n; }
+
+// injected faults: the mask set by infft_inject_faults, initially from INFFT_FAULT
+// (a comma-separated list of alloc, launch, cg)
+static std::atomic<int> g_fault_mask{-1};
+
+static unsigned fault_mask_from_env() {
+    const char* e = getenv("INFFT_FAULT");
+    unsigned m = 0;
+    if (e) {
+        if (strstr(e, "alloc")) m |= FAULT_ALLOC;
+        if (strstr(e, "launch")) m |= FAULT_LAUNCH;
+        if (strstr(e, "cg")) m |= FAULT_CG;
+    }
+    return m;
+}
+
+bool fault(unsigned bit) {
+    int m = g_fault_mask.load(std::memory_order_relaxed);
+    if (m < 0) {
+        m = (int)fault_mask_from_env();
+        g_fault_mask.store(m, std::memory_order_relaxed);
+    }
+    return (m & (int)bit) != 0;
+}
 
 static std::mutex g_pool_mu;
 static cudaMemPool_t g_pool[64] = {};
@@ -76,6 +101,10 @@ void pool_free(void* ptr, cudaStream_t st) {
 infft_status dev_alloc(infft_plan_s* p, void** ptr, size_t bytes) {
     *ptr = nullptr;
     if (bytes == 0) return INFFT_OK;
+    if (fault(FAULT_ALLOC)) {
+        set_error("injected allocation failure (%zu bytes)", bytes);
+        return INFFT_ENOMEM;
+    }
     if (p && p->pooled) {
         INFFT_TRY(pool_alloc(ptr, bytes, p->pool_stream));
         p->device_bytes += bytes;
@@ -372,18 +401,31 @@ static infft_status build_plan(infft_plan_s* p, const double* x_in, cudaStream_t
     // points to the device
     double* x_dev = nullptr;
     const bool x_on_dev = is_device_pointer(x_in);
+    // temporaries of the build, returned to the pool in stream order on every exit path
+    struct Temps {
+        cudaStream_t st;
+        std::vector<void*> v;
+        ~Temps() { for (void* q : v) pool_free(q, st); }
+    } temps{st, {}};
     INFFT_TRY(pool_alloc((void**)&x_dev, (size_t)N * d * sizeof(double), st));
+    temps.v.push_back(x_dev);
     INFFT_CUDA(cudaMemcpyAsync(x_dev, x_in, (size_t)N * d * sizeof(double),
                                x_on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     uint32_t *key = nullptr, *cellrm = nullptr;
     double *u64 = nullptr, *xw = nullptr;
     int *count = nullptr, *fill = nullptr, *order = nullptr;
     INFFT_TRY(pool_alloc((void**)&key, (size_t)N * 4, st));
+    temps.v.push_back(key);
     INFFT_TRY(pool_alloc((void**)&cellrm, (size_t)N * 4, st));
+    temps.v.push_back(cellrm);
     INFFT_TRY(pool_alloc((void**)&u64, (size_t)N * d * 8, st));
+    temps.v.push_back(u64);
     INFFT_TRY(pool_alloc((void**)&xw, (size_t)N * d * 8, st));
+    temps.v.push_back(xw);
     INFFT_TRY(pool_alloc((void**)&fill, (size_t)(nkeys + 1) * 4, st));
+    temps.v.push_back(fill);
     INFFT_TRY(pool_alloc((void**)&order, (size_t)N * 4, st));
+    temps.v.push_back(order);
     INFFT_TRY(dev_alloc(p, (void**)&p->cell_start, (size_t)(nkeys + 1) * 4));
     count = p->cell_start;
     INFFT_CUDA(cudaMemsetAsync(count, 0, (size_t)(nkeys + 1) * 4, st));
@@ -437,8 +479,7 @@ static infft_status build_plan(infft_plan_s* p, const double* x_in, cudaStream_t
     INFFT_CUDA(cudaMemcpyAsync(p->tile_items, tile_items.data(), (size_t)(ntiles + 1) * 4, cudaMemcpyHostToDevice,
                                st));
 
-    for (void* q : {(void*)x_dev, (void*)key, (void*)cellrm, (void*)u64, (void*)xw, (void*)fill, (void*)order})
-        pool_free(q, st);
+
 
     // tables
     INFFT_TRY(dev_alloc(p, &p->dinv, (size_t)p->M * R_sz));
@@ -523,6 +564,8 @@ infft_status infft_plan(int d, int M, int64_t N, const double* x, double sigma, 
                         infft_plan_t* out) {
     return plan_create(d, M, N, x, sigma, m, flags, (cudaStream_t)stream, false, out);
 }
+
+void infft_inject_faults(unsigned mask) { g_fault_mask.store((int)(mask & 7u), std::memory_order_relaxed); }
 
 void infft_destroy(infft_plan_t p) {
     if (!p) return;

@@ -432,6 +432,7 @@ static infft_status weights_impl(infft_plan_s* p, int max_iter, double rel_tol, 
     }
     INFFT_CUDA(cudaStreamSynchronize(st));
     if (iters_out) *iters_out = it;
+    if (fault(FAULT_CG)) conv = false;   // injected: report non-convergence (weights stored)
     if (!conv) {
         set_error("CG did not reach rel_tol %g in %d iterations", rel_tol, max_iter);
         return INFFT_ENOTCONV;

@@ -43,6 +43,7 @@ class Request:
     t_done: float = 0.0
     out: Any = None
     batch_size: int = 0
+    error: Optional[BaseException] = None   # set when its point set could not be built
 
 
 @dataclasses.dataclass
@@ -162,6 +163,7 @@ class Server:
         self._n_parked = 0
         self.inflight: List[tuple] = []
         self.completed: List[Request] = []
+        self.failed: List[Request] = []       # requests whose point set failed to build
         self.stats = collections.Counter()
         self._retry: collections.deque = collections.deque()   # sets waiting for memory, FIFO
         self._deferred_keys: set = set()
@@ -286,9 +288,16 @@ class Server:
                 key, plan, err = self._ready.get_nowait()
             except queue.Empty:
                 break
-            if err is not None:
-                raise err
             self._reserved_total -= self.reserved.pop(key, 0)
+            if err is not None:   # the requests of this set fail; the loop goes on
+                failed = self.parked.pop(key, [])
+                self._n_parked -= len(failed)
+                t = now()
+                for r in failed:
+                    r.error, r.t_done = err, t
+                    self.failed.append(r)
+                self.stats["failed_sets"] += 1
+                continue
             self.plans[key] = plan
             self.plan_used[key] = now()
             self.plan_size[key] = self.be.plan_bytes(plan)

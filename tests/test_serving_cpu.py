@@ -186,3 +186,22 @@ def test_reconstruction_streams_outrank_the_precompute_stream():
     s = Server(FakeBackend(), streams=3)
     assert all(st[1] < s._pstream[1] for st in s.streams)
     s.close()
+
+
+def test_failed_builds_fail_their_requests_and_the_loop_goes_on():
+    class Flaky(FakeBackend):
+        def build_plan(self, ps, stream):
+            if ps.key == 1:
+                raise RuntimeError("INFFT_ENOMEM: injected allocation failure")
+            return super().build_plan(ps, stream)
+
+    be = Flaky(latency=2)
+    s = Server(be, max_batch=8, streams=2)
+    for ps in sets(3):
+        s.register(ps)
+    run(s, [Request(rid=i, key=i % 3, f=i) for i in range(12)])
+    assert sorted(r.rid for r in s.completed) == [i for i in range(12) if i % 3 != 1]
+    assert sorted(r.rid for r in s.failed) == [1, 4, 7, 10]
+    assert all(isinstance(r.error, RuntimeError) for r in s.failed)
+    assert s.stats["failed_sets"] == 1 and not s.reserved
+    s.close()
