@@ -181,6 +181,12 @@ infft_status infft_get_weights(infft_plan_t plan, void* w, void* stream);
  */
 infft_status infft_optimize_B(infft_plan_t plan, unsigned opts, double* max_col_residual, void* stream);
 
+/* infft_set_bopt -- restore B_opt coefficients saved by infft_get_bopt for a plan with the
+ * same points and parameters (N x S^d complex128, caller's point order, host or device),
+ * so that a cached precompute (Algorithm 4.3) need not be repeated; the plan is then
+ * ready for INFFT_MODE_BOPT and infft_inverse_adjoint.  Synchronises. */
+infft_status infft_set_bopt(infft_plan_t plan, const void* coeff, void* stream);
+
 /* infft_get_bopt -- copy B_opt coefficients, N x S^d complex128 (S = 2m+2, slot
  * s_t holds column floor(M_sigma x_t) - m + s_t), caller's point order. */
 infft_status infft_get_bopt(infft_plan_t plan, void* coeff, void* stream);

@@ -46,6 +46,7 @@ _SIGS = {
     "infft_get_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "infft_optimize_B": (C.c_int, [C.c_void_p, C.c_uint, C.POINTER(C.c_double), C.c_void_p]),
     "infft_get_bopt": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "infft_set_bopt": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "infft_adjoint": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "infft_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "infft_inverse_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -200,7 +201,8 @@ class Plan:
 
     def __init__(self, x, M: int, sigma: float = 2.0, m: int = 4, precision: str = "fp32",
                  window: str = "kb", stream=None, pooled: bool = False):
-        self.precision = precision
+        self.precision, self.window = precision, window
+        self.has_weights = self.has_bopt = False
         flags = {"fp32": FP32, "fp64": FP64}[precision] | (POOLED if pooled else 0)
         flags |= {"kb": WIN_KB, "bspline": WIN_BSPLINE, "dirichlet": WIN_DIRICHLET}[window]
         if isinstance(x, np.ndarray):
@@ -248,10 +250,12 @@ class Plan:
         s, res, it = infft_weights(self.handle, max_iter, rel_tol, m_cg, _stream(stream), opts)
         if check and s not in (OK, ENOTCONV):
             _check(s)
+        self.has_weights = self.has_weights or s in (OK, ENOTCONV)
         return {"status": s, "residual_inf": res, "iters": it}
 
     def set_weights(self, w, stream=None):
         _check(load().infft_set_weights(self.handle, _ptr(w), _stream(stream)))
+        self.has_weights = True
 
     def get_weights(self, stream=None) -> np.ndarray:
         w = np.empty(self.N, dtype=np.complex128)
@@ -261,7 +265,14 @@ class Plan:
     def optimize_B(self, opts: int = 0, stream=None):
         s, res = infft_optimize_B(self.handle, opts, _stream(stream))
         _check(s)
+        self.has_bopt = True
         return res
+
+    def set_bopt(self, coeff, stream=None):
+        """Restore B_opt coefficients from get_bopt (N x (2m+2)^d complex128)."""
+        c = np.ascontiguousarray(coeff, dtype=np.complex128) if isinstance(coeff, np.ndarray) else coeff
+        _check(load().infft_set_bopt(self.handle, _ptr(c), _stream(stream)))
+        self.has_bopt = True
 
     def get_bopt(self, stream=None) -> np.ndarray:
         S = 2 * self.m + 2

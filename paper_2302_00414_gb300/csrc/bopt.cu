@@ -325,6 +325,16 @@ __global__ void k_bopt_unsort(const cx<double>* __restrict__ a, const int* __res
     }
 }
 
+// caller order -> sorted order (the inverse of k_bopt_unsort)
+__global__ void k_bopt_sort_in(const cx<double>* __restrict__ in, const int* __restrict__ perm, long long N, int NS,
+                               cx<double>* __restrict__ a) {
+    const long long total = N * NS;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const long long i = e / NS;
+        a[e] = in[(long long)perm[i] * NS + e % NS];
+    }
+}
+
 static infft_status optimize_impl(infft_plan_s* p, unsigned opts, double* max_res, cudaStream_t st,
                                   std::vector<void*>& tmp) {
     BoptGeom g;
@@ -440,6 +450,36 @@ infft_status infft_optimize_B(infft_plan_t p, unsigned opts, double* max_col_res
     cudaStreamSynchronize((cudaStream_t)stream);
     for (void* q : tmp) cudaFree(q);
     return s;
+}
+
+infft_status infft_set_bopt(infft_plan_t p, const void* coeff, void* stream) {
+    if (!p || !coeff) { set_error("null argument"); return INFFT_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    p->pool_stream = st;
+    const int NS = ipow(2 * p->m + 2, p->d);
+    const long long nent = (long long)p->N * NS;
+    const size_t bytes = (size_t)nent * 16;
+    if (!p->coef64) INFFT_TRY(dev_alloc(p, (void**)&p->coef64, bytes));
+    if (!p->coef) INFFT_TRY(dev_alloc(p, &p->coef, (size_t)nent * (p->fp64 ? 16 : 8)));
+    const bool dev = is_device_pointer(coeff);
+    const void* src = coeff;
+    void* staged = nullptr;
+    if (!dev) {
+        INFFT_CUDA(cudaMalloc(&staged, bytes));
+        INFFT_CUDA(cudaMemcpyAsync(staged, coeff, bytes, cudaMemcpyHostToDevice, st));
+        src = staged;
+    }
+    k_bopt_sort_in<<<1024, 256, 0, st>>>((const cx<double>*)src, p->perm, p->N, NS, (cx<double>*)p->coef64);
+    INFFT_LAUNCHED();
+    const int cb = (int)std::min<long long>((nent + 255) / 256, 65535LL * 16);
+    if (p->fp64) k_bopt_convert<double><<<cb, 256, 0, st>>>((cx<double>*)p->coef64, nent, (cx<double>*)p->coef);
+    else k_bopt_convert<float><<<cb, 256, 0, st>>>((cx<double>*)p->coef64, nent, (cx<float>*)p->coef);
+    INFFT_LAUNCHED();
+    INFFT_CUDA(cudaStreamSynchronize(st));
+    if (staged) cudaFree(staged);
+    p->has_bopt = true;
+    p->bopt_window = p->window;
+    return INFFT_OK;
 }
 
 infft_status infft_get_bopt(infft_plan_t p, void* coeff, void* stream) {
