@@ -81,7 +81,6 @@ enum {
     INFFT_MODE_BOPT = 2      /* h = D^* F^* B_opt^* f      (Algorithm 4.4)            */
 };
 
-/* options of infft_optimize_B */
 /* options of infft_weights_opts */
 enum {
     INFFT_WEIGHTS_AUTO = 0,       /* Toeplitz products where they apply, else NFFT products  */
@@ -89,6 +88,7 @@ enum {
     INFFT_WEIGHTS_TOEPLITZ = 2    /* convolution form of A^*A (second kind only)             */
 };
 
+/* options of infft_optimize_B */
 enum {
     INFFT_BOPT_PATTERN_2M2 = 0,   /* 2m+2 consecutive indices per coordinate (default)       */
     INFFT_BOPT_PATTERN_PAPER = 1, /* the index set I_{Msigma,m}(x_j) of eq. indexset_x         */
