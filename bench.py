@@ -195,7 +195,7 @@ def profiled_traffic():
     if not os.path.exists(summary):
         return None
     h = hashlib.sha256()
-    for f in ("spread2d.cu", "common.cuh", "jobset.cuh"):
+    for f in ("spread2d.cuh", "common.cuh", "jobset.cuh"):
         with open(os.path.join(ROOT, "paper_2302_00414_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     want, value = None, None

@@ -8,7 +8,7 @@
 
 namespace infft {
 
-// Launch the d = 2 register-row spread when every job qualifies (same m in 2..7, P <= 32,
+// Launch the d = 2 register-row spread when every job qualifies (same m in 2..8, P <= 32,
 // all window modes or all B_opt); *used tells whether it did.
 template <class R>
 infft_status spread2d_try(JobSet<R>& js, cudaStream_t st, bool* used);

@@ -1,10 +1,30 @@
-// Two-dimensional spreading kernel (register rows) and its launcher.
+// Two-dimensional spreading kernel (register rows) and its launcher, instantiated for
+// float32 and float64 in their own translation units (compiled in parallel).
+#pragma once
+
 #include <algorithm>
+#include <cstdint>
+#include <cstdlib>
 #include <type_traits>
 
 #include "spread.cuh"
 
 namespace infft {
+
+// cp.async of one aligned element of B bytes (4, 8 or 16) from global to shared memory
+template <int B>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// bytes of the per-warp prefetch slots (w, u pairs, perm, cell of 32 points); a multiple of 16
+template <class R, bool PF>
+__host__ __device__ constexpr size_t spread2d_slot_bytes() {
+    return PF ? 32 * (sizeof(cx<R>) + 2 * sizeof(R) + 2 * sizeof(int)) : 0;
+}
 
 // ---------------------------------------------------------------------------------------
 // Two-dimensional spreading with the accumulators in registers.  One warp per work
@@ -16,8 +36,12 @@ namespace infft {
 // (coefficient c_j psi_y[k] broadcast, times psi_x of its column), and when the next
 // point starts lower it stores the rows that no later point can reach.  Every padded
 // cell is stored exactly once, no shared-memory read-modify-write, no atomics.
-// Window values are computed once per point while staging 32 points per warp.
-template <class R, int MM, bool BOPT>
+// Window values are computed once per point while staging 32 points per warp.  With PF
+// (window modes on grids too small to hide load latency with other warps) the sorted
+// data of the next 32 points (perm, cell, u, w) are copied to shared memory with cp.async
+// while the current ones are spread, so that staging waits only on the gather of the
+// samples f.
+template <class R, int MM, bool BOPT, bool PF>
 // float32 with m <= 4: at most 80 registers, so six 4-warp blocks (24 warps) share an SM
 // (batched d = 2, m = 4: spread 0.607 -> 0.574 ms); m = 5 would spill at that bound
 __global__ void __launch_bounds__(128, (sizeof(R) == 4 && MM <= 4 && !BOPT) ? 6 : 1)
@@ -37,7 +61,12 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4 && MM <= 4 && !BOPT) ? 6 
     const int P = J.P, Ms = J.Ms, T = J.T;
 
     unsigned char* base = smem_raw + (size_t)warp * js.smem_per_warp;
-    cx<R>* cy = reinterpret_cast<cx<R>*>(base);            // [32][WE] c_j psi_y (window mode)
+    // prefetch slots (PF only): lane l copies, and later reads, the data of its own point only
+    cx<R>* pf_w = reinterpret_cast<cx<R>*>(base);               // [32]    w (DCF)
+    R* pf_u = reinterpret_cast<R*>(pf_w + 32);                  // [32][2] fractional offsets
+    int* pf_perm = reinterpret_cast<int*>(pf_u + 64);           // [32]    caller's index
+    uint32_t* pf_cell = reinterpret_cast<uint32_t*>(pf_perm + 32);  // [32] base cell
+    cx<R>* cy = reinterpret_cast<cx<R>*>(base + spread2d_slot_bytes<R, PF>());  // [32][WE] c_j psi_y (window mode)
     // psi_x of each staged point laid out by padded column, zero off the point's taps, so
     // that lane l reads its column's weight directly (row pitch 33: conflict-free both ways)
     R* psx = reinterpret_cast<R*>(cy + 32 * WE);            // [32][33] psi_x by column
@@ -58,16 +87,31 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4 && MM <= 4 && !BOPT) ? 6 
     cx<R>* dst = J.padded + (size_t)it * P * P;
     const bool col_ok = lane < P;
     const int logMs = 31 - __clz(Ms);
+    const bool dcf = J.mode == INFFT_MODE_DCF;
+    auto prefetch = [&](int c) {   // the sorted data of points c .. c + 31 of the item
+        if (c + lane < item.z) {
+            const size_t i = (size_t)item.y + c + lane;
+            cp_async<4>(pf_perm + lane, J.perm + i);
+            cp_async<4>(pf_cell + lane, J.cell + i);
+            if (!BOPT) {
+                cp_async<2 * sizeof(R)>(pf_u + 2 * lane, J.u + 2 * i);
+                if (dcf) cp_async<sizeof(cx<R>)>(pf_w + lane, J.w + i);
+            }
+        }
+        cp_async_commit();
+    };
+    if (PF && item.z > 0) prefetch(0);
 
     for (int c0 = 0; c0 < item.z; c0 += 32) {
         const int np = min(32, item.z - c0);
         __syncwarp();
+        if (PF) cp_async_wait_all();
         if (lane < np) {
             const int i = item.y + c0 + lane;
-            const int j = __ldg(J.perm + i);
+            const int j = PF ? pf_perm[lane] : __ldg(J.perm + i);
             cx<R> fv = J.in[j];
-            if (J.mode == INFFT_MODE_DCF) fv = mul(J.w[i], fv);
-            const uint32_t cl = __ldg(J.cell + i);
+            if (dcf) fv = mul(PF ? pf_w[lane] : J.w[i], fv);
+            const uint32_t cl = PF ? pf_cell[lane] : __ldg(J.cell + i);
             const int cxl = (int)(cl & (uint32_t)(Ms - 1)), cyl = (int)(cl >> logMs);
             meta[lane * 3 + 0] = cyl - ty * T;
             meta[lane * 3 + 1] = cxl - tx * T;
@@ -75,7 +119,8 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4 && MM <= 4 && !BOPT) ? 6 
             if (BOPT) {
                 cst[lane] = fv;
             } else {
-                const R uy = J.u[(size_t)i * 2 + 0], ux = J.u[(size_t)i * 2 + 1];
+                const R uy = PF ? pf_u[2 * lane + 0] : J.u[(size_t)i * 2 + 0];
+                const R ux = PF ? pf_u[2 * lane + 1] : J.u[(size_t)i * 2 + 1];
                 R wy[W], wx[W];
                 bool done = false;
                 if constexpr (F32) {
@@ -103,7 +148,8 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4 && MM <= 4 && !BOPT) ? 6 
                 cy[lane * WE + W] = mk<R>(0, 0);
             }
         }
-        __syncwarp();
+        __syncwarp();   // orders every read of the prefetch slots before their refill
+        if (PF && c0 + 32 < item.z) prefetch(c0 + 32);
         // The points are sorted by base row, so the chunk splits into runs of equal oy
         // (found by one ballot): the rows above a run are stored once per run, and the
         // points of a run only add their taps.  A test of the rows held per point cost
@@ -181,12 +227,12 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4 && MM <= 4 && !BOPT) ? 6 
     }
 }
 
-// register-row spreading for d = 2 when every job has the same m (2..7) and P <= 32
-template <class R, int MM, bool BOPT>
+// register-row spreading for d = 2 when every job has the same m (2..8) and P <= 32
+template <class R, int MM, bool BOPT, bool PF>
 static infft_status launch_spread2d_m(JobSet<R>& js, cudaStream_t st) {
     constexpr int W = 2 * MM + 1;
     constexpr int WE = W + 1;
-    size_t spw = 32 * WE * sizeof(cx<R>) + 32 * 33 * sizeof(R) + 96 * sizeof(int) + 32 * sizeof(cx<R>) +
+    size_t spw = spread2d_slot_bytes<R, PF>() + 32 * WE * sizeof(cx<R>) + 32 * 33 * sizeof(R) + 96 * sizeof(int) + 32 * sizeof(cx<R>) +
                  (WPOLY_DEG + 1) * wpoly_stride(W) * sizeof(float);
     spw = (spw + 15) & ~(size_t)15;
     js.smem_per_warp = (int)spw;
@@ -194,23 +240,51 @@ static infft_status launch_spread2d_m(JobSet<R>& js, cudaStream_t st) {
     const int nitems = js.pre_items[js.njobs];
     if (nitems == 0) return INFFT_OK;
     const size_t smem = spw * js.wpb;
-    INFFT_CUDA(cudaFuncSetAttribute(k_spread2d<R, MM, BOPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_spread2d<R, MM, BOPT><<<(nitems + js.wpb - 1) / js.wpb, 32 * js.wpb, smem, st>>>(js);
+    INFFT_CUDA(cudaFuncSetAttribute(k_spread2d<R, MM, BOPT, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_spread2d<R, MM, BOPT, PF><<<(nitems + js.wpb - 1) / js.wpb, 32 * js.wpb, smem, st>>>(js);
     INFFT_LAUNCHED();
     return INFFT_OK;
 }
 
-template <class R, bool BOPT>
+template <class R, bool BOPT, bool PF>
 static infft_status launch_spread2d(JobSet<R>& js, cudaStream_t st, int m) {
     switch (m) {
-        case 2: return launch_spread2d_m<R, 2, BOPT>(js, st);
-        case 3: return launch_spread2d_m<R, 3, BOPT>(js, st);
-        case 4: return launch_spread2d_m<R, 4, BOPT>(js, st);
-        case 5: return launch_spread2d_m<R, 5, BOPT>(js, st);
-        case 6: return launch_spread2d_m<R, 6, BOPT>(js, st);
-        case 7: return launch_spread2d_m<R, 7, BOPT>(js, st);
-        default: return launch_spread2d_m<R, 8, BOPT>(js, st);
+        case 2: return launch_spread2d_m<R, 2, BOPT, PF>(js, st);
+        case 3: return launch_spread2d_m<R, 3, BOPT, PF>(js, st);
+        case 4: return launch_spread2d_m<R, 4, BOPT, PF>(js, st);
+        case 5: return launch_spread2d_m<R, 5, BOPT, PF>(js, st);
+        case 6: return launch_spread2d_m<R, 6, BOPT, PF>(js, st);
+        case 7: return launch_spread2d_m<R, 7, BOPT, PF>(js, st);
+        default: return launch_spread2d_m<R, 8, BOPT, PF>(js, st);
     }
+}
+
+static bool aligned(const void* p, size_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+
+// Fewer work items than eight warps per SM leave the staging's load latency exposed: then
+// the prefetching form runs, when the copies it makes are aligned element by element.
+// INFFT_SPREAD2D_PREFETCH=0 or 1 picks the form regardless of size (both give the same
+// sums in the same order).
+template <class R>
+static bool spread2d_prefetch(const JobSet<R>& js) {
+    const char* env = getenv("INFFT_SPREAD2D_PREFETCH");
+    if (env && env[0] == '0') return false;
+    if (!(env && env[0] == '1')) {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (js.pre_items[js.njobs] >= 8 * nsm) return false;
+    }
+    for (int j = 0; j < js.njobs; ++j) {
+        const Job<R>& J = js.job[j];
+        if (!aligned(J.perm, 4) || !aligned(J.cell, 4) || !aligned(J.u, 2 * sizeof(R)) ||
+            (J.mode == INFFT_MODE_DCF && !aligned(J.w, sizeof(cx<R>))))
+            return false;
+    }
+    return true;
 }
 
 template <class R>
@@ -235,10 +309,9 @@ infft_status spread2d_try(JobSet<R>& js, cudaStream_t st, bool* used) {
     *used = false;
     if (!spread2d_eligible(js, &m, &bopt)) return INFFT_OK;
     *used = true;
-    return bopt ? launch_spread2d<R, true>(js, st, m) : launch_spread2d<R, false>(js, st, m);
+    if (bopt) return launch_spread2d<R, true, false>(js, st, m);
+    return spread2d_prefetch(js) ? launch_spread2d<R, false, true>(js, st, m)
+                                 : launch_spread2d<R, false, false>(js, st, m);
 }
-
-template infft_status spread2d_try<float>(JobSet<float>&, cudaStream_t, bool*);
-template infft_status spread2d_try<double>(JobSet<double>&, cudaStream_t, bool*);
 
 }  // namespace infft
