@@ -20,6 +20,18 @@ __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Float32 window modes with m <= 4 spread two points at a time, one per half-warp: lane l
+// owns columns 2 (l mod 16) and 2 (l mod 16) + 1 for the points of its half, and the two
+// halves' partial sums of a cell are added when its row is stored.  A 16-byte load of
+// broadcast coefficients costs two shared-memory wavefronts either way, so each then
+// serves two points; shared-memory wavefronts bound this kernel.
+template <class R, int MM, bool BOPT>
+__host__ __device__ constexpr bool spread2d_pair() { return sizeof(R) == 4 && !BOPT && MM <= 4; }
+// row pitch of the staged psi_x: odd (33) when each lane reads one column, even (34) for
+// the 8-byte column pairs of the paired form
+template <class R, int MM, bool BOPT>
+__host__ __device__ constexpr int spread2d_pitch() { return spread2d_pair<R, MM, BOPT>() ? 34 : 33; }
+
 // bytes of the per-warp prefetch slots (w, u pairs, perm, cell of 32 points); a multiple of 16
 template <class R, bool PF>
 __host__ __device__ constexpr size_t spread2d_slot_bytes() {
@@ -44,12 +56,15 @@ __host__ __device__ constexpr size_t spread2d_slot_bytes() {
 template <class R, int MM, bool BOPT, bool PF>
 // float32 with m <= 4: at most 80 registers, so six 4-warp blocks (24 warps) share an SM
 // (batched d = 2, m = 4: spread 0.607 -> 0.574 ms); m = 5 would spill at that bound
-__global__ void __launch_bounds__(128, (sizeof(R) == 4 && MM <= 4 && !BOPT) ? 6 : 1)
+__global__ void __launch_bounds__(128, spread2d_pair<R, MM, BOPT>() ? 5 : (sizeof(R) == 4 && MM <= 4 && !BOPT) ? 6 : 1)
     k_spread2d(const __grid_constant__ JobSet<R> js) {
     constexpr int W = 2 * MM + 1;              // window taps per axis
     constexpr int WE = W + 1;                  // even stride of the staged rows (16-byte loads)
     constexpr int WR = BOPT ? W + 1 : W;       // rows held in registers
     constexpr bool F32 = sizeof(R) == 4;
+    constexpr bool PAIR = spread2d_pair<R, MM, BOPT>();
+    constexpr int PX = spread2d_pitch<R, MM, BOPT>();
+    constexpr int NC = PAIR ? 2 : 1;           // columns per lane
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gitem = blockIdx.x * js.wpb + warp;
@@ -68,9 +83,9 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4 && MM <= 4 && !BOPT) ? 6 
     uint32_t* pf_cell = reinterpret_cast<uint32_t*>(pf_perm + 32);  // [32] base cell
     cx<R>* cy = reinterpret_cast<cx<R>*>(base + spread2d_slot_bytes<R, PF>());  // [32][WE] c_j psi_y (window mode)
     // psi_x of each staged point laid out by padded column, zero off the point's taps, so
-    // that lane l reads its column's weight directly (row pitch 33: conflict-free both ways)
-    R* psx = reinterpret_cast<R*>(cy + 32 * WE);            // [32][33] psi_x by column
-    int* meta = reinterpret_cast<int*>(psx + 32 * 33);      // [32][3]  oy, ox, sorted index
+    // that each lane reads its columns' weights directly (conflict-free both ways)
+    R* psx = reinterpret_cast<R*>(cy + 32 * WE);            // [32][PX] psi_x by column
+    int* meta = reinterpret_cast<int*>(psx + 32 * PX);      // [32][3]  oy, ox, sorted index
     cx<R>* cst = reinterpret_cast<cx<R>*>(meta + 96);       // [32]     c_j (B_opt mode)
     float* poly = reinterpret_cast<float*>(cst + 32);       // [(WPOLY_DEG+1) * WP] window polynomial (16-byte rows)
     const bool use_poly = F32 && !BOPT && J.wpoly != nullptr;
@@ -80,12 +95,33 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4 && MM <= 4 && !BOPT) ? 6 
 
     const int ty = item.x / J.ntile, tx = item.x % J.ntile;
     using V2 = typename std::conditional<F32, float2, double2>::type;
-    V2 acc[WR];  // (re, im) of the rows r0 .. r0 + WR - 1 of this lane's column
+    // (re, im) of the rows r0 .. r0 + WR - 1 of this lane's columns: acc[NC k + c] is row
+    // r0 + k of the lane's column c
+    V2 acc[NC * WR];
 #pragma unroll
-    for (int k = 0; k < WR; ++k) { acc[k].x = R(0); acc[k].y = R(0); }
-    int r0 = 0;  // padded row held in acc[0]
+    for (int k = 0; k < NC * WR; ++k) { acc[k].x = R(0); acc[k].y = R(0); }
+    int r0 = 0;  // padded row held in acc[0 .. NC - 1]
     cx<R>* dst = J.padded + (size_t)it * P * P;
     const bool col_ok = lane < P;
+    // store row r0 (no later point reaches it) and move the held rows up by one
+    auto flush_row = [&]() {
+        if constexpr (PAIR) {
+            float4 v = make_float4(acc[0].x, acc[0].y, acc[1].x, acc[1].y);
+            v.x += __shfl_xor_sync(0xffffffffu, v.x, 16);
+            v.y += __shfl_xor_sync(0xffffffffu, v.y, 16);
+            v.z += __shfl_xor_sync(0xffffffffu, v.z, 16);
+            v.w += __shfl_xor_sync(0xffffffffu, v.w, 16);
+            // P and the item's base are even: the column pair is 16-byte aligned
+            if (lane < 16 && 2 * lane < P) *reinterpret_cast<float4*>(dst + (size_t)r0 * P + 2 * lane) = v;
+        } else {
+            if (col_ok) dst[(size_t)r0 * P + lane] = mk<R>(acc[0].x, acc[0].y);
+        }
+#pragma unroll
+        for (int k = 0; k < NC * (WR - 1); ++k) acc[k] = acc[k + NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) { acc[NC * (WR - 1) + c].x = R(0); acc[NC * (WR - 1) + c].y = R(0); }
+        ++r0;
+    };
     const int logMs = 31 - __clz(Ms);
     const bool dcf = J.mode == INFFT_MODE_DCF;
     auto prefetch = [&](int c) {   // the sorted data of points c .. c + 31 of the item
@@ -136,7 +172,7 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4 && MM <= 4 && !BOPT) ? 6 
                         wx[s] = tap_weight<R>(J.window, ux, s, MM, J.inv_m, J.beta);
                     }
                 }
-                R* row = psx + lane * 33;
+                R* row = psx + lane * PX;
 #pragma unroll
                 for (int c = 0; c < 32; ++c) row[c] = R(0);
                 const int oxl = cxl - tx * T;   // ox + s <= T - 1 + 2m = P - 1 < 32
@@ -160,15 +196,36 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4 && MM <= 4 && !BOPT) ? 6 
         while (p < np) {
             const int oy = __shfl_sync(0xffffffffu, my_oy, p);
             // store the rows above oy: no later point reaches them
-            while (r0 < oy) {
-                if (col_ok) dst[(size_t)r0 * P + lane] = mk<R>(acc[0].x, acc[0].y);
-#pragma unroll
-                for (int k = 0; k < WR - 1; ++k) acc[k] = acc[k + 1];
-                acc[WR - 1].x = R(0);
-                acc[WR - 1].y = R(0);
-                ++r0;
-            }
+            while (r0 < oy) flush_row();
             const int q = 32 - __clz(__ballot_sync(0xffffffffu, my_oy == oy));
+            if constexpr (PAIR) {
+                // points p + h of each pair go to half h; at an odd run end the second
+                // half adds zeros (the first point's taps times a zero weight)
+                const int half = lane >> 4, hl = lane & 15;
+#pragma unroll 2
+                for (; p < q; p += 2) {
+                    const int pp = p + half;
+                    const bool act = pp < q;
+                    const int pr = act ? pp : p;
+                    float2 wv = *reinterpret_cast<const float2*>(psx + pr * PX + 2 * hl);
+                    if (!act) wv = make_float2(0.f, 0.f);
+                    const float2 wa = make_float2(wv.x, wv.x), wb = make_float2(wv.y, wv.y);
+                    const float4* cp4 = reinterpret_cast<const float4*>(cy + pr * WE);
+#pragma unroll
+                    for (int k2 = 0; k2 < WE / 2; ++k2) {
+                        const float4 c = cp4[k2];
+                        const float2 c0 = make_float2(c.x, c.y), c1 = make_float2(c.z, c.w);
+                        acc[4 * k2] = __ffma2_rn(c0, wa, acc[4 * k2]);
+                        acc[4 * k2 + 1] = __ffma2_rn(c0, wb, acc[4 * k2 + 1]);
+                        if (2 * k2 + 1 < W) {
+                            acc[4 * k2 + 2] = __ffma2_rn(c1, wa, acc[4 * k2 + 2]);
+                            acc[4 * k2 + 3] = __ffma2_rn(c1, wb, acc[4 * k2 + 3]);
+                        }
+                    }
+                }
+                p = q;
+                continue;
+            }
             // float32: four points per unrolled step let the loads of the next points
             // overlap the current FMAs (0.573 -> 0.506 ms before the runs); float64 keeps
             // its registers for the accumulators
@@ -191,7 +248,7 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4 && MM <= 4 && !BOPT) ? 6 
                         }
                     }
                 } else {
-                    const R wx = psx[p * 33 + lane];
+                    const R wx = psx[p * PX + lane];
                     const cx<R>* cp = cy + p * WE;
                     if constexpr (F32) {
                         // two complex coefficients per 16-byte broadcast load, one packed
@@ -217,14 +274,7 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4 && MM <= 4 && !BOPT) ? 6 
         }
     }
     // remaining rows (including rows no point reached)
-    while (r0 < P) {
-        if (col_ok) dst[(size_t)r0 * P + lane] = mk<R>(acc[0].x, acc[0].y);
-#pragma unroll
-        for (int k = 0; k < WR - 1; ++k) acc[k] = acc[k + 1];
-        acc[WR - 1].x = R(0);
-        acc[WR - 1].y = R(0);
-        ++r0;
-    }
+    while (r0 < P) flush_row();
 }
 
 // register-row spreading for d = 2 when every job has the same m (2..8) and P <= 32
@@ -232,7 +282,7 @@ template <class R, int MM, bool BOPT, bool PF>
 static infft_status launch_spread2d_m(JobSet<R>& js, cudaStream_t st) {
     constexpr int W = 2 * MM + 1;
     constexpr int WE = W + 1;
-    size_t spw = spread2d_slot_bytes<R, PF>() + 32 * WE * sizeof(cx<R>) + 32 * 33 * sizeof(R) + 96 * sizeof(int) + 32 * sizeof(cx<R>) +
+    size_t spw = spread2d_slot_bytes<R, PF>() + 32 * WE * sizeof(cx<R>) + 32 * spread2d_pitch<R, MM, BOPT>() * sizeof(R) + 96 * sizeof(int) + 32 * sizeof(cx<R>) +
                  (WPOLY_DEG + 1) * wpoly_stride(W) * sizeof(float);
     spw = (spw + 15) & ~(size_t)15;
     js.smem_per_warp = (int)spw;
