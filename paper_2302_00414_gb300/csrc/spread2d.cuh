@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(128, spread2d_pair<R, MM, BOPT>() ? 5 : (sizeo
 #pragma unroll
     for (int k = 0; k < NC * WR; ++k) { acc[k].x = R(0); acc[k].y = R(0); }
     int r0 = 0;  // padded row held in acc[0 .. NC - 1]
+    int old_ox = -1;   // first column of this lane's taps in its psi_x row, -1: row not zeroed yet
     cx<R>* dst = J.padded + (size_t)it * P * P;
     const bool col_ok = lane < P;
     // store row r0 (no later point reaches it) and move the held rows up by one
@@ -173,9 +174,16 @@ __global__ void __launch_bounds__(128, spread2d_pair<R, MM, BOPT>() ? 5 : (sizeo
                     }
                 }
                 R* row = psx + lane * PX;
+                // the row is zero off the taps the lane wrote last time: clear those only
+                if (old_ox < 0) {
 #pragma unroll
-                for (int c = 0; c < 32; ++c) row[c] = R(0);
+                    for (int c = 0; c < 32; ++c) row[c] = R(0);
+                } else {
+#pragma unroll
+                    for (int s = 0; s < W; ++s) row[old_ox + s] = R(0);
+                }
                 const int oxl = cxl - tx * T;   // ox + s <= T - 1 + 2m = P - 1 < 32
+                old_ox = oxl;
 #pragma unroll
                 for (int s = 0; s < W; ++s) {
                     cy[lane * WE + s] = scale(fv, wy[s]);
