@@ -27,6 +27,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // serves two points; shared-memory wavefronts bound this kernel.
 template <class R, int MM, bool BOPT>
 __host__ __device__ constexpr bool spread2d_pair() { return sizeof(R) == 4 && !BOPT && MM <= 4; }
+template <class R>
+constexpr bool spread2d_pair_m(int m) { return sizeof(R) == 4 && m <= 4; }   // window modes
 // row pitch of the staged psi_x: odd (33) when each lane reads one column, even (34) for
 // the 8-byte column pairs of the paired form
 template <class R, int MM, bool BOPT>
@@ -49,7 +51,7 @@ __host__ __device__ constexpr size_t spread2d_slot_bytes() {
 // point starts lower it stores the rows that no later point can reach.  Every padded
 // cell is stored exactly once, no shared-memory read-modify-write, no atomics.
 // Window values are computed once per point while staging 32 points per warp.  With PF
-// (window modes on grids too small to hide load latency with other warps) the sorted
+// (window modes: the paired form, and grids too small to hide load latency) the sorted
 // data of the next 32 points (perm, cell, u, w) are copied to shared memory with cp.async
 // while the current ones are spread, so that staging waits only on the gather of the
 // samples f.
@@ -319,15 +321,17 @@ static infft_status launch_spread2d(JobSet<R>& js, cudaStream_t st, int m) {
 
 static bool aligned(const void* p, size_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
 
-// Fewer work items than eight warps per SM leave the staging's load latency exposed: then
-// the prefetching form runs, when the copies it makes are aligned element by element.
-// INFFT_SPREAD2D_PREFETCH=0 or 1 picks the form regardless of size (both give the same
-// sums in the same order).
+// The paired form (float32, m <= 4) always prefetches (batched d = 2, m = 4: spread 0.389 ->
+// 0.383 ms); the one-point forms prefetch only when there are fewer work items than eight
+// warps per SM (with many items, other warps hide the staging's load latency and the copies
+// cost more than they save: 0.428 -> 0.444 ms for the one-point float32 form).  Either way
+// the copies must be aligned element by element.  INFFT_SPREAD2D_PREFETCH=0 or 1 picks the
+// form regardless (both give the same sums in the same order).
 template <class R>
-static bool spread2d_prefetch(const JobSet<R>& js) {
+static bool spread2d_prefetch(const JobSet<R>& js, int m) {
     const char* env = getenv("INFFT_SPREAD2D_PREFETCH");
     if (env && env[0] == '0') return false;
-    if (!(env && env[0] == '1')) {
+    if (!(env && env[0] == '1') && !spread2d_pair_m<R>(m)) {
         int dev = 0, nsm = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -368,7 +372,7 @@ infft_status spread2d_try(JobSet<R>& js, cudaStream_t st, bool* used) {
     if (!spread2d_eligible(js, &m, &bopt)) return INFFT_OK;
     *used = true;
     if (bopt) return launch_spread2d<R, true, false>(js, st, m);
-    return spread2d_prefetch(js) ? launch_spread2d<R, false, true>(js, st, m)
+    return spread2d_prefetch(js, m) ? launch_spread2d<R, false, true>(js, st, m)
                                  : launch_spread2d<R, false, false>(js, st, m);
 }
 
