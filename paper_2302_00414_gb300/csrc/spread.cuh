@@ -3,10 +3,28 @@
 // and interpolation for d = 2, 3 (Algorithm 2.1 step 3).
 #pragma once
 
+#include <cstdlib>
+
 #include "internal.h"
 #include "jobset.cuh"
 
 namespace infft {
+
+// cp.async of one aligned element of B bytes (4, 8 or 16) from global to shared memory
+template <int B>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// the environment's choice of a kernel form: 0 or 1 from the variable's first character,
+// -1 when it is unset or says neither
+inline int env_form(const char* name) {
+    const char* e = getenv(name);
+    return (e && e[0] == '0') ? 0 : (e && e[0] == '1') ? 1 : -1;
+}
 
 // Launch the d = 2 register-row spread when every job qualifies (same m in 2..8, P <= 32,
 // all window modes or all B_opt); *used tells whether it did.

@@ -4,21 +4,11 @@
 
 #include <algorithm>
 #include <cstdint>
-#include <cstdlib>
 #include <type_traits>
 
 #include "spread.cuh"
 
 namespace infft {
-
-// cp.async of one aligned element of B bytes (4, 8 or 16) from global to shared memory
-template <int B>
-__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(B) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Float32 window modes with m <= 4 spread two points at a time, one per half-warp: lane l
 // owns columns 2 (l mod 16) and 2 (l mod 16) + 1 for the points of its half, and the two
@@ -329,9 +319,9 @@ static bool aligned(const void* p, size_t a) { return ((uintptr_t)p & (a - 1)) =
 // form regardless (both give the same sums in the same order).
 template <class R>
 static bool spread2d_prefetch(const JobSet<R>& js, int m) {
-    const char* env = getenv("INFFT_SPREAD2D_PREFETCH");
-    if (env && env[0] == '0') return false;
-    if (!(env && env[0] == '1') && !spread2d_pair_m<R>(m)) {
+    const int env = env_form("INFFT_SPREAD2D_PREFETCH");
+    if (env == 0) return false;
+    if (env != 1 && !spread2d_pair_m<R>(m)) {
         int dev = 0, nsm = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {

@@ -1,5 +1,9 @@
-// Three-dimensional spreading kernel (register-held cells per base cell) and its launcher.
+// Three-dimensional spreading kernel (register-held cells per base cell) and its launcher,
+// instantiated for float32 and float64 in their own translation units (compiled in parallel).
+#pragma once
+
 #include <algorithm>
+#include <cstdint>
 #include <type_traits>
 
 #include "spread.cuh"
@@ -19,10 +23,19 @@ namespace infft {
 // The z-planes of the shared tile are PZ >= P^2 cells apart with PZ = W (mod 16), so the
 // cells of 16 consecutive pairs, at q + const (mod 16) in 8-byte units, fall into
 // distinct bank pairs: no bank conflicts.  The tile is written out densely (P^3).
+// With PF the sorted data of the next 32 points (perm, cell, u, w) are copied to shared
+// memory with cp.async while the current ones are spread: with five warps per SM, other
+// warps cannot hide the staging's global loads.
 __host__ __device__ constexpr int spread3d_plane(int P, int W) { return P * P + (((W - P * P) % 16) + 16) % 16; }
 constexpr int SPREAD3D_T = 8;
 
-template <class R, int MM>
+// bytes of the per-warp prefetch slots (w, u triples, perm, cell of 32 points); a multiple of 16
+template <class R, bool PF>
+__host__ __device__ constexpr size_t spread3d_slot_bytes() {
+    return PF ? 32 * (sizeof(cx<R>) + 3 * sizeof(R) + 2 * sizeof(int)) : 0;
+}
+
+template <class R, int MM, bool PF>
 __global__ void __launch_bounds__(64) k_spread3d(const __grid_constant__ JobSet<R> js) {
     constexpr int W = 2 * MM + 1;
     constexpr int WE = W + 1;                  // even stride of the staged rows
@@ -43,7 +56,12 @@ __global__ void __launch_bounds__(64) k_spread3d(const __grid_constant__ JobSet<
     const int Ms = J.Ms, nt = J.ntile;
 
     unsigned char* base = smem_raw + (size_t)warp * js.smem_per_warp;
-    V2* pad = reinterpret_cast<V2*>(base);                             // [P][PZ]
+    // prefetch slots (PF only): lane l copies, and later reads, the data of its own point only
+    cx<R>* pf_w = reinterpret_cast<cx<R>*>(base);                      // [32]    w (DCF)
+    R* pf_u = reinterpret_cast<R*>(pf_w + 32);                         // [32][3] fractional offsets
+    int* pf_perm = reinterpret_cast<int*>(pf_u + 96);                  // [32]    caller's index
+    uint32_t* pf_cell = reinterpret_cast<uint32_t*>(pf_perm + 32);     // [32]    base cell
+    V2* pad = reinterpret_cast<V2*>(base + spread3d_slot_bytes<R, PF>());  // [P][PZ]
     V2* cyv = pad + ((SC + 1) & ~1);                                   // [32][WE] c_j psi_y
     R* psz = reinterpret_cast<R*>(cyv + 32 * WE);                      // [32][WE]
     R* psx = psz + 32 * WE;                                            // [32][WE]
@@ -73,21 +91,37 @@ __global__ void __launch_bounds__(64) k_spread3d(const __grid_constant__ JobSet<
 #pragma unroll
         for (int s = 0; s < W; ++s) { v[r][s].x = R(0); v[r][s].y = R(0); }
     int cur = -1;
+    const bool dcf = J.mode == INFFT_MODE_DCF;
+    auto prefetch = [&](int c) {   // the sorted data of points c .. c + 31 of the item
+        if (c + lane < item.z) {
+            const size_t i = (size_t)item.y + c + lane;
+            cp_async<4>(pf_perm + lane, J.perm + i);
+            cp_async<4>(pf_cell + lane, J.cell + i);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) cp_async<sizeof(R)>(pf_u + 3 * lane + a, J.u + 3 * i + a);
+            if (dcf) cp_async<sizeof(cx<R>)>(pf_w + lane, J.w + i);
+        }
+        cp_async_commit();
+    };
+    if (PF && item.z > 0) prefetch(0);
 
     for (int c0 = 0; c0 < item.z; c0 += 32) {
         const int np = min(32, item.z - c0);
         __syncwarp();
+        if (PF) cp_async_wait_all();
         if (lane < np) {
             const int i = item.y + c0 + lane;
-            const int j = __ldg(J.perm + i);
+            const int j = PF ? pf_perm[lane] : __ldg(J.perm + i);
             cx<R> fv = J.in[j];
-            if (J.mode == INFFT_MODE_DCF) fv = mul(J.w[i], fv);
-            const uint32_t cl = __ldg(J.cell + i);
+            if (dcf) fv = mul(PF ? pf_w[lane] : J.w[i], fv);
+            const uint32_t cl = PF ? pf_cell[lane] : __ldg(J.cell + i);
             const int cxl = (int)(cl & (uint32_t)(Ms - 1));
             const int cyl = (int)((cl >> logMs) & (uint32_t)(Ms - 1));
             const int czl = (int)(cl >> (2 * logMs));
             meta[lane] = (czl - tz * T) * PZ + (cyl - ty * T) * P + (cxl - tx * T);
-            const R uz = J.u[(size_t)i * 3 + 0], uy = J.u[(size_t)i * 3 + 1], ux = J.u[(size_t)i * 3 + 2];
+            const R uz = PF ? pf_u[3 * lane + 0] : J.u[(size_t)i * 3 + 0];
+            const R uy = PF ? pf_u[3 * lane + 1] : J.u[(size_t)i * 3 + 1];
+            const R ux = PF ? pf_u[3 * lane + 2] : J.u[(size_t)i * 3 + 2];
             R wz[W], wy[W], wx[W];
             bool done = false;
             if constexpr (F32) {
@@ -113,7 +147,8 @@ __global__ void __launch_bounds__(64) k_spread3d(const __grid_constant__ JobSet<
                 psx[lane * WE + s] = wx[s];
             }
         }
-        __syncwarp();
+        __syncwarp();   // orders every read of the prefetch slots before their refill
+        if (PF && c0 + 32 < item.z) prefetch(c0 + 32);
         for (int p = 0; p < np; ++p) {
             const int b0 = meta[p];
             if (b0 != cur) {   // uniform across the warp
@@ -165,14 +200,15 @@ __global__ void __launch_bounds__(64) k_spread3d(const __grid_constant__ JobSet<
         for (int e = lane; e < P2; e += 32) dst[(size_t)z * P2 + e] = pad[z * PZ + e];
 }
 
-// three-dimensional spreading in window modes when every job has the same m (1..7)
-template <class R, int MM>
+// three-dimensional spreading in window modes when every job has the same m (1..6)
+template <class R, int MM, bool PF>
 static infft_status launch_spread3d_m(JobSet<R>& js, cudaStream_t st) {
     constexpr int W = 2 * MM + 1;
     constexpr int WE = W + 1;
     constexpr int P = SPREAD3D_T + 2 * MM;
     const size_t cells = (size_t)P * spread3d_plane(P, W);
-    size_t spw = ((cells + 1) & ~(size_t)1) * sizeof(cx<R>) + 32 * WE * (sizeof(cx<R>) + 2 * sizeof(R)) +
+    size_t spw = spread3d_slot_bytes<R, PF>() +
+                 ((cells + 1) & ~(size_t)1) * sizeof(cx<R>) + 32 * WE * (sizeof(cx<R>) + 2 * sizeof(R)) +
                  32 * sizeof(int) + (WPOLY_DEG + 1) * wpoly_stride(W) * sizeof(float);
     spw = (spw + 15) & ~(size_t)15;
     const size_t smem_cap = 200 * 1024;
@@ -185,8 +221,8 @@ static infft_status launch_spread3d_m(JobSet<R>& js, cudaStream_t st) {
     const int nitems = js.pre_items[js.njobs];
     if (nitems == 0) return INFFT_OK;
     const size_t smem = spw * js.wpb;
-    INFFT_CUDA(cudaFuncSetAttribute(k_spread3d<R, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_spread3d<R, MM><<<(nitems + js.wpb - 1) / js.wpb, 32 * js.wpb, smem, st>>>(js);
+    INFFT_CUDA(cudaFuncSetAttribute(k_spread3d<R, MM, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_spread3d<R, MM, PF><<<(nitems + js.wpb - 1) / js.wpb, 32 * js.wpb, smem, st>>>(js);
     INFFT_LAUNCHED();
     return INFFT_OK;
 }
@@ -205,16 +241,32 @@ static bool spread3d_eligible(const JobSet<R>& js, int* m_out) {
     return true;
 }
 
-template <class R>
+template <class R, bool PF>
 static infft_status launch_spread3d(JobSet<R>& js, cudaStream_t st, int m) {
     switch (m) {
-        case 1: return launch_spread3d_m<R, 1>(js, st);
-        case 2: return launch_spread3d_m<R, 2>(js, st);
-        case 3: return launch_spread3d_m<R, 3>(js, st);
-        case 4: return launch_spread3d_m<R, 4>(js, st);
-        case 5: return launch_spread3d_m<R, 5>(js, st);
-        default: return launch_spread3d_m<R, 6>(js, st);
+        case 1: return launch_spread3d_m<R, 1, PF>(js, st);
+        case 2: return launch_spread3d_m<R, 2, PF>(js, st);
+        case 3: return launch_spread3d_m<R, 3, PF>(js, st);
+        case 4: return launch_spread3d_m<R, 4, PF>(js, st);
+        case 5: return launch_spread3d_m<R, 5, PF>(js, st);
+        default: return launch_spread3d_m<R, 6, PF>(js, st);
     }
+}
+
+static bool aligned3(const void* p, size_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+
+// The prefetching form runs unless INFFT_SPREAD3D_PREFETCH=0 (both forms give the same sums
+// in the same order) or a copy it would make is misaligned.
+template <class R>
+static bool spread3d_prefetch(const JobSet<R>& js) {
+    if (env_form("INFFT_SPREAD3D_PREFETCH") == 0) return false;
+    for (int j = 0; j < js.njobs; ++j) {
+        const Job<R>& J = js.job[j];
+        if (!aligned3(J.perm, 4) || !aligned3(J.cell, 4) || !aligned3(J.u, sizeof(R)) ||
+            (J.mode == INFFT_MODE_DCF && !aligned3(J.w, sizeof(cx<R>))))
+            return false;
+    }
+    return true;
 }
 
 template <class R>
@@ -223,10 +275,7 @@ infft_status spread3d_try(JobSet<R>& js, cudaStream_t st, bool* used) {
     *used = false;
     if (!spread3d_eligible(js, &m)) return INFFT_OK;
     *used = true;
-    return launch_spread3d<R>(js, st, m);
+    return spread3d_prefetch(js) ? launch_spread3d<R, true>(js, st, m) : launch_spread3d<R, false>(js, st, m);
 }
-
-template infft_status spread3d_try<float>(JobSet<float>&, cudaStream_t, bool*);
-template infft_status spread3d_try<double>(JobSet<double>&, cudaStream_t, bool*);
 
 }  // namespace infft

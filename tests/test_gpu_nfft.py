@@ -225,3 +225,26 @@ def test_spread2d_prefetch_forms_equal(prec, mode, monkeypatch):
     assert np.array_equal(out["0"], out["1"])
     ref = NF.adjoint_nfft(x, f * w if mode == "dcf" else f, M, sigma, m)
     assert rel(out["1"], ref) < (1e-5 if prec == "fp32" else 1e-12)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("gen", ["random", "clustered"])
+def test_spread3d_prefetch_forms_equal(prec, gen, monkeypatch):
+    """The d = 3 spread with and without the next points' data prefetched makes the same sums
+    in the same order (bit for bit), within the bounds of the oracle's Algorithm 2.4."""
+    L, torch = lib_or_skip()
+    M, sigma, m = 16, 2.0, 4
+    x = points(3, 3000, gen, 31)
+    f = inputs.samples_complex(len(x), 32)
+    w = inputs.rng(33).uniform(0.5, 1.5, len(x)) / len(x)
+    cdt = torch.complex64 if prec == "fp32" else torch.complex128
+    p = L.Plan(x, M, sigma, m, prec)
+    p.set_weights(w.astype(np.complex128))
+    fd = to_dev(torch, f, cdt)
+    out = {}
+    for form in ("0", "1"):
+        monkeypatch.setenv("INFFT_SPREAD3D_PREFETCH", form)
+        out[form] = p.adjoint(fd, mode=L.MODE_DCF).cpu().numpy()
+    assert np.array_equal(out["0"], out["1"])
+    ref = NF.adjoint_nfft(x, f * w, M, sigma, m)
+    assert rel(out["1"], ref) < (1e-5 if prec == "fp32" else 1e-12)
