@@ -410,7 +410,7 @@ def run_ours(args, rank, world, dist):
         "roofline": {"bound": "hbm", "kernel": "k_spread2d", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": profiled_traffic(),
                      "peak_kind": peak_kind, "algorithmic_bytes": int(spread_bytes),
-                     "note": "bound on chip (ncu: shared-memory wavefronts 66% of peak, issue 56%, DRAM 9%), see profiles/"},
+                     "note": "bound on chip (ncu: shared-memory wavefronts 71% of peak, issue 59%, DRAM 9%), see profiles/"},
         "e2e": {"value": e2e_rate, "unit": "recon/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(kernels_per_step * args.steps),
         "clocks": clocks,
