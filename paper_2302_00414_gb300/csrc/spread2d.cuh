@@ -33,7 +33,7 @@ __host__ __device__ constexpr size_t spread2d_slot_bytes() {
 // ---------------------------------------------------------------------------------------
 // Two-dimensional spreading with the accumulators in registers.  One warp per work
 // item; lane l owns column l of the item's P x P padded tile (P = T + 2m, one more for
-// B_opt slots; P <= 32).
+// B_opt slots; P <= 32), or a column pair in the paired form above.
 // The item's points are sorted by base row, so the rows a point can touch,
 // [oy, oy + 2m] (padded coordinates; one more row for B_opt slots), only move down:
 // each lane keeps those rows of its column in registers, adds the point's taps
@@ -46,9 +46,9 @@ __host__ __device__ constexpr size_t spread2d_slot_bytes() {
 // while the current ones are spread, so that staging waits only on the gather of the
 // samples f.
 template <class R, int MM, bool BOPT, bool PF>
-// float32 with m <= 4: at most 80 registers, so six 4-warp blocks (24 warps) share an SM
-// (batched d = 2, m = 4: spread 0.607 -> 0.574 ms); m = 5 would spill at that bound
-__global__ void __launch_bounds__(128, spread2d_pair<R, MM, BOPT>() ? 5 : (sizeof(R) == 4 && MM <= 4 && !BOPT) ? 6 : 1)
+// the paired form holds 2 (2m + 1) complex accumulators: at most 96 registers, so five 4-warp
+// blocks (20 warps) share an SM (the one-point form ran six at 80 registers)
+__global__ void __launch_bounds__(128, spread2d_pair<R, MM, BOPT>() ? 5 : 1)
     k_spread2d(const __grid_constant__ JobSet<R> js) {
     constexpr int W = 2 * MM + 1;              // window taps per axis
     constexpr int WE = W + 1;                  // even stride of the staged rows (16-byte loads)
@@ -347,6 +347,7 @@ static bool spread2d_eligible(const JobSet<R>& js, int* m_out, bool* bopt_out) {
     for (int j = 0; j < js.njobs; ++j) {
         const Job<R>& J = js.job[j];
         if (J.d != 2 || J.m != m || (J.mode == INFFT_MODE_BOPT) != bopt || J.P > 32) return false;
+        if (!bopt && spread2d_pair_m<R>(m) && (J.P & 1)) return false;   // paired rows: 16-byte stores
     }
     if (m < 2 || m > 8) return false;   // m = 8 with window taps only: P = 16 + 16 <= 32
     *m_out = m;
