@@ -198,6 +198,11 @@ infft_status infft_get_bopt(infft_plan_t plan, void* coeff, void* stream);
  *   mode = INFFT_MODE_BOPT : Algorithm 4.4, h = D^* F^* B_opt^* f (needs B_opt).
  *   f    : N complex samples (host or device), caller's point order.
  *   fhat : M^d complex result (host or device), C order over I_M.
+ * The spreading kernels for d = 2 and d = 3 copy the next points' sorted data to shared
+ * memory while they spread the current ones (d = 3: always; d = 2: float32 with m <= 4,
+ * and grids with fewer work items than eight warps per SM).  INFFT_SPREAD2D_PREFETCH and
+ * INFFT_SPREAD3D_PREFETCH in the environment ("0" off, "1" on) override that choice; the
+ * sums and their order, and so the results bit for bit, are the same either way.
  */
 infft_status infft_adjoint(infft_plan_t plan, int mode, const void* f, void* fhat, void* stream);
 
