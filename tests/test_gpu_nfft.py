@@ -248,3 +248,31 @@ def test_spread3d_prefetch_forms_equal(prec, gen, monkeypatch):
     assert np.array_equal(out["0"], out["1"])
     ref = NF.adjoint_nfft(x, f * w, M, sigma, m)
     assert rel(out["1"], ref) < (1e-5 if prec == "fp32" else 1e-12)
+
+
+@pytest.mark.parametrize("m", [2, 3, 5])
+@pytest.mark.parametrize("gen", ["random", "clustered"])
+def test_fp32_d2_other_m_match_oracle_algorithm(m, gen):
+    """Float32 d = 2 spreading at m = 2, 3 (two points per warp) and m = 5 (one point per warp)
+    follows the oracle's Algorithm 2.4 to float32 rounding, on random points and on clustered
+    ones (long runs of equal base row, odd run lengths)."""
+    L, torch = lib_or_skip()
+    M, sigma = 32, 2.0
+    x = points(2, 3001, gen, 41)
+    f = inputs.samples_complex(len(x), 42)
+    p = L.Plan(x, M, sigma, m, "fp32")
+    h = p.adjoint(to_dev(torch, f, torch.complex64)).cpu().numpy()
+    assert rel(h, NF.adjoint_nfft(x, f, M, sigma, m)) < 1e-5
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 33])
+def test_fp32_d2_tiny_point_counts(N):
+    """Work items of one to 33 points (a lone point leaves the second half-warp idle) give the
+    oracle's Algorithm 2.4 to float32 rounding."""
+    L, torch = lib_or_skip()
+    M, sigma, m = 16, 2.0, 4
+    x = inputs.random_points(N, 2, 43 + N)
+    f = inputs.samples_complex(N, 44 + N)
+    p = L.Plan(x, M, sigma, m, "fp32")
+    h = p.adjoint(to_dev(torch, f, torch.complex64)).cpu().numpy()
+    assert rel(h, NF.adjoint_nfft(x, f, M, sigma, m)) < 1e-5
