@@ -56,6 +56,34 @@ def column_members(x: np.ndarray, Ms: int, m: int, pattern=PATTERN_2M2):
     return cols
 
 
+def column_members_of(x: np.ndarray, Ms: int, m: int, cols, pattern=PATTERN_2M2):
+    """I_{Ms,m}(l) (eq. indexset_l) for the listed flat columns only, in the layout of
+    ``column_members``: flat column -> list of (j, slot tuple), j ascending.
+
+    Point j belongs to column l when, along every coordinate, the offset
+    (l_t - (floor(Ms x_t) - m)) mod Ms names one of its slots s_t < 2m+2 and that
+    slot is in the pattern.  Vectorised over the points, for large point sets."""
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    N, d = x.shape
+    cand, valid = point_slots(x, Ms, m, pattern)
+    S = slot_count(m)
+    first = cand[:, :, 0]                          # floor(Ms x_t) - m, not reduced
+    out = {}
+    for col in cols:
+        lt = column_l(int(col), Ms, d)
+        s = np.mod(lt[None, :] - first, Ms)        # slot of column l along each axis
+        ok = np.all(s < S, axis=1)
+        js = np.nonzero(ok)[0]
+        mem = []
+        for j in js:
+            slots = tuple(int(v) for v in s[j])
+            if all(valid[j, t, st] for t, st in enumerate(slots)):
+                mem.append((int(j), slots))
+        if mem:
+            out[int(col)] = mem
+    return out
+
+
 def column_l(col: int, Ms: int, d: int) -> np.ndarray:
     """The multi-index l in I_Ms of a flat column index."""
     l = []

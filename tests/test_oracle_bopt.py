@@ -110,6 +110,79 @@ def test_real_field_variant_is_no_better_than_complex():
         assert e_c[col] <= e_r[col] + 1e-12 * scale
 
 
+def _real_columns(n_cols=12):
+    """Columns of a small random point set with their members' points and l."""
+    x, M, sigma, m, Ms = _setup(N=90, M=6, m=2, seed=17)
+    members = BO.column_members(x, Ms, m, BO.PATTERN_2M2)
+    cols = [c for c in sorted(members) if len(members[c]) >= 2][:n_cols]
+    for col in cols:
+        js = np.array([j for j, _ in members[col]])
+        yield x[js], BO.column_l(col, Ms, 2), M, Ms, m
+
+
+def real_field_pin_holds() -> bool:
+    """Reading R6, real field: b in R^n minimises ||H b - rhs||_2 exactly when the gradient
+    of the objective over real b, 2 Re(H^* (H b - rhs)), vanishes (the objective is a convex
+    quadratic in b).  Stated from the first-order conditions of the real least-squares
+    problem of eqs. 4.10/4.11, not from the oracle's stacked solve; b must also be real."""
+    for xm, l, M, Ms, m in _real_columns():
+        b, eps = BO.solve_column(xm, l, M, Ms, m, W.KB, field="real")
+        H = BO.matrix_H(xm, M)
+        r = BO.rhs(l, M, Ms, m, W.KB)
+        grad = np.real(np.conj(H).T @ (H @ b - r))
+        if np.max(np.abs(b.imag)) != 0.0:
+            return False
+        if np.max(np.abs(grad)) > 1e-10 * np.linalg.norm(np.conj(H).T @ r):
+            return False
+        if abs(eps - np.linalg.norm(H @ b - r) ** 2) > 1e-12 * np.linalg.norm(r) ** 2:
+            return False
+    return True
+
+
+def test_real_field_first_order_conditions():
+    assert real_field_pin_holds()
+
+
+def test_real_field_single_member_closed_form():
+    """One member: min over real b of ||h b - r||^2 is b = Re(h^* r) / ||h||^2, with
+    ||h||^2 = |I_M| and h^* r = sum_k w^(k) exp(2 pi i k (x_j - l/Ms)) written out here
+    as a direct sum over I_M."""
+    M, Ms, m = 8, 16, 3
+    xm = np.array([[0.137, -0.402]])
+    l = np.array([2, -6])
+    b, _ = BO.solve_column(xm, l, M, Ms, m, W.KB, field="real")
+    k1 = np.arange(-M // 2, M // 2)
+    hr = 0.0 + 0.0j
+    for a in k1:
+        for c in k1:
+            wk = W.what1(W.KB, np.array([a]), M, Ms, m)[0] * W.what1(W.KB, np.array([c]), M, Ms, m)[0]
+            hr += wk * np.exp(2j * np.pi * (a * (xm[0, 0] - l[0] / Ms) + c * (xm[0, 1] - l[1] / Ms)))
+    assert abs(b[0] - hr.real / M ** 2) < 1e-13 * abs(hr)
+
+
+def test_real_field_matches_numerical_minimiser():
+    """A generic minimiser (BFGS on the real objective, started at 0) reaches the same b."""
+    from scipy.optimize import minimize
+    for xm, l, M, Ms, m in list(_real_columns(4)):
+        b, eps = BO.solve_column(xm, l, M, Ms, m, W.KB, field="real")
+        H = BO.matrix_H(xm, M)
+        r = BO.rhs(l, M, Ms, m, W.KB)
+        obj = lambda v: float(np.linalg.norm(H @ v - r) ** 2)
+        jac = lambda v: 2.0 * np.real(np.conj(H).T @ (H @ v - r))
+        res = minimize(obj, np.zeros(len(b)), jac=jac, method="BFGS", options={"gtol": 1e-14, "maxiter": 10000})
+        assert res.fun >= eps - 1e-10 * np.linalg.norm(r) ** 2
+        assert abs(res.fun - eps) <= 1e-8 * np.linalg.norm(r) ** 2
+
+
+@pytest.mark.parametrize("pattern", [BO.PATTERN_2M2, BO.PATTERN_PAPER])
+def test_column_members_of_matches_full_enumeration(pattern):
+    x, M, sigma, m, Ms = _setup(N=150, M=6, m=2, seed=5)
+    full = BO.column_members(x, Ms, m, pattern)
+    assert BO.column_members_of(x, Ms, m, range(Ms * Ms), pattern) == full
+    some = [3, 40, 77, 143]
+    assert BO.column_members_of(x, Ms, m, some, pattern) == {c: full[c] for c in some if c in full}
+
+
 # --- inverse adjoint NFFT (Remark 4.6) --------------------------------------------------
 
 def test_inverse_adjoint_is_the_product_B_F_D():

@@ -74,3 +74,32 @@ def test_weight_mutants_fail(monkeypatch, mutant):
         orig = WT.weights
         monkeypatch.setattr(WT, "weights", lambda x, M, rcond=1e-13: orig(x, M // 2, rcond))
     assert not _weights_pin()
+
+
+# --- the real-field least squares of B_opt (reading R6) --------------------------------
+
+def _real_solve_mutant(orig, how):
+    """solve_column with one plausible mistake in its real-field branch only."""
+    def solve(xm, l, M, Ms, m, kind, field="complex", rcond=1e-12):
+        if field != "real":
+            return orig(xm, l, M, Ms, m, kind, field, rcond)
+        if how == "conj_block":      # imaginary block stacked with the wrong sign
+            return orig(-xm, l, M, Ms, m, kind, field, rcond)
+        b, e = orig(xm, l, M, Ms, m, kind, field, rcond)
+        if how == "sign":
+            b = -b
+        elif how == "zero":
+            b = np.zeros_like(b)
+        elif how == "re_of_complex":  # the real part of the complex solution
+            b = orig(xm, l, M, Ms, m, kind, "complex", rcond)[0].real.astype(np.complex128)
+        return b, e
+    return solve
+
+
+@pytest.mark.parametrize("how", ["sign", "zero", "re_of_complex", "conj_block"])
+def test_real_field_mutants_fail(monkeypatch, how):
+    from oracle import bopt as BO
+    from tests.test_oracle_bopt import real_field_pin_holds
+    assert real_field_pin_holds()
+    monkeypatch.setattr(BO, "solve_column", _real_solve_mutant(BO.solve_column, how))
+    assert not real_field_pin_holds()
