@@ -292,9 +292,10 @@ void infft_batch_destroy(infft_batch_t batch);
  * library holds until the process exits.  A plan whose scratch would exceed 32 MiB is
  * rejected with INFFT_EINVAL and a message giving both sizes.  The call allocates
  * nothing: no cudaMalloc, no cudaFree, no allocating library routine.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current and caches it; make that first call before any stream
- * capture.  All calls share the one array and every call overwrites all the scratch it
+ * The first call in a CUDA context (on each device, and again after a cudaDeviceReset has
+ * replaced the device's primary context) looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and caches it per context; make that
+ * first call before any stream capture.  Mode and state errors are those of infft_adjoint.  All calls share the one array and every call overwrites all the scratch it
  * reads, so nothing carries over between calls -- but calls that overlap on the GPU
  * (different streams, or different host threads) race on it and must be serialised by
  * the caller.
@@ -304,6 +305,7 @@ infft_status infft_adjoint_noalloc(infft_plan_t plan, int mode, const void* f, v
 /* Accessors. */
 int64_t infft_plan_N(infft_plan_t plan);
 int infft_plan_Msigma(infft_plan_t plan);
+int infft_plan_work_items(infft_plan_t plan);        /* work items (tile, point range) of the spread */
 size_t infft_plan_device_bytes(infft_plan_t plan);   /* device memory held by the plan */
 const char* infft_last_error(void);
 void infft_destroy(infft_plan_t plan);

@@ -63,6 +63,7 @@ _SIGS = {
     "infft_batch_destroy": (None, [C.c_void_p]),
     "infft_plan_N": (C.c_int64, [C.c_void_p]),
     "infft_plan_Msigma": (C.c_int, [C.c_void_p]),
+    "infft_plan_work_items": (C.c_int, [C.c_void_p]),
     "infft_plan_device_bytes": (C.c_size_t, [C.c_void_p]),
     "infft_last_error": (C.c_char_p, []),
     "infft_destroy": (None, [C.c_void_p]),
@@ -226,6 +227,11 @@ class Plan:
     @property
     def complex_dtype(self):
         return np.complex64 if self.precision == "fp32" else np.complex128
+
+    @property
+    def work_items(self) -> int:
+        """Number of work items (tile, point range) the plan's spreading kernels run."""
+        return int(load().infft_plan_work_items(self.handle))
 
     @property
     def device_bytes(self) -> int:

@@ -138,6 +138,10 @@ infft_status dev_alloc(infft_plan_s* p, void** ptr, size_t bytes);
 // in-place exclusive prefix sum of n ints on the device (stream ordered)
 infft_status scan_exclusive(int* data, long long n, cudaStream_t st);
 bool is_device_pointer(const void* ptr);
+// the preconditions of a reconstruction mode on a plan (INFFT_EINVAL for an unknown mode,
+// INFFT_ESTATE for DCF without weights, BOPT without B_opt, or a window mode on a
+// Dirichlet-window plan); shared by every entry point that takes a mode
+infft_status check_mode(const infft_plan_s* p, int mode);
 
 // Build the Job descriptors of a list of plans for one transform each.
 template <class R>

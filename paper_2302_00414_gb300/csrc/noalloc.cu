@@ -19,31 +19,71 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[INFFT_NOALLOC_S
 
 namespace {
 
-constexpr int kMaxDevices = 64;
+// The device address of g_noalloc_scratch belongs to the module loaded in one CUDA
+// context.  A device reset (cudaDeviceReset) destroys the primary context; the next call
+// runs in a new context, where the module may sit elsewhere.  So the address is cached
+// per context, keyed by the driver's unique context id (cuCtxGetId), and looked up again
+// whenever the current context has an id not seen before.
+struct CachedAddress {
+    unsigned long long ctx_id;
+    void* addr;
+};
+constexpr int kMaxCached = 64;
 std::mutex g_mutex;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
+CachedAddress g_cache[kMaxCached];
+int g_ncache = 0;
 
-// Device address of g_noalloc_scratch on the current device.  In host code the
-// symbol only names a host-side stand-in, so its address is looked up once per
-// device, with that device current, and cached.
-infft_status scratch_address(void** out) {
-    int dev = 0;
-    INFFT_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) {
-        infft::set_error("device index %d out of range", dev);
-        return INFFT_EINVAL;
-    }
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            infft::set_error("cudaGetSymbolAddress(g_noalloc_scratch) failed: %s", cudaGetErrorString(e));
+typedef int (*ctx_get_current_fn)(void**);
+typedef int (*ctx_get_id_fn)(void*, unsigned long long*);
+
+// id of the current context through the driver entry points (no link to libcuda)
+infft_status current_context_id(unsigned long long* id) {
+    static ctx_get_current_fn get_current = nullptr;
+    static ctx_get_id_fn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        INFFT_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1));
+        INFFT_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2));
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+            infft::set_error("driver entry points cuCtxGetCurrent / cuCtxGetId not found");
             return INFFT_ECUDA;
         }
-        g_scratch_addr[dev] = p;
+        get_current = (ctx_get_current_fn)f1;
+        get_id = (ctx_get_id_fn)f2;
     }
-    *out = g_scratch_addr[dev];
+    void* ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx || get_id(ctx, id) != 0) {
+        infft::set_error("no current CUDA context");
+        return INFFT_ECUDA;
+    }
+    return INFFT_OK;
+}
+
+// Device address of g_noalloc_scratch in the current context.  In host code the symbol
+// only names a host-side stand-in, so the address is looked up with cudaGetSymbolAddress,
+// once per context (the device current), and cached.
+infft_status scratch_address(void** out) {
+    // bind the current device's primary context to this thread (cudaSetDevice initialises
+    // it and makes it current; nothing is allocated)
+    int dev = 0;
+    INFFT_CUDA(cudaGetDevice(&dev));
+    INFFT_CUDA(cudaSetDevice(dev));
+    unsigned long long id = 0;
+    INFFT_TRY(current_context_id(&id));
+    std::lock_guard<std::mutex> lock(g_mutex);
+    for (int i = 0; i < g_ncache; ++i)
+        if (g_cache[i].ctx_id == id) { *out = g_cache[i].addr; return INFFT_OK; }
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        infft::set_error("cudaGetSymbolAddress(g_noalloc_scratch) failed: %s", cudaGetErrorString(e));
+        return INFFT_ECUDA;
+    }
+    if (g_ncache < kMaxCached) g_cache[g_ncache++] = CachedAddress{id, p};
+    else g_cache[id % kMaxCached] = CachedAddress{id, p};
+    *out = p;
     return INFFT_OK;
 }
 
@@ -91,12 +131,7 @@ infft_status infft_adjoint_noalloc(infft_plan_t plan, int mode, const void* f, v
         infft::set_error("infft_adjoint_noalloc: null argument");
         return INFFT_EINVAL;
     }
-    if (mode == INFFT_MODE_DCF && !plan->has_weights) { infft::set_error("DCF mode needs weights"); return INFFT_ESTATE; }
-    if (mode == INFFT_MODE_BOPT && !plan->has_bopt) { infft::set_error("BOPT mode needs B_opt"); return INFFT_ESTATE; }
-    if (mode < 0 || mode > 2 || (mode != INFFT_MODE_BOPT && plan->window == infft::WK_DIRICHLET)) {
-        infft::set_error("infft_adjoint_noalloc: mode %d not valid for this plan", mode);
-        return INFFT_EINVAL;
-    }
+    INFFT_TRY(infft::check_mode(plan, mode));   // the same codes and messages as infft_adjoint
     if (!infft::is_device_pointer(f) || !infft::is_device_pointer(fhat)) {
         infft::set_error("infft_adjoint_noalloc: f and fhat must be device pointers");
         return INFFT_EINVAL;

@@ -592,9 +592,14 @@ int infft_debug_info(infft_plan_t p, int which) {
 
 int64_t infft_plan_N(infft_plan_t p) { return p ? p->N : -1; }
 int infft_plan_Msigma(infft_plan_t p) { return p ? p->Ms : -1; }
+int infft_plan_work_items(infft_plan_t p) { return p ? p->nitems : -1; }
 size_t infft_plan_device_bytes(infft_plan_t p) { return p ? p->device_bytes : 0; }
 
-static infft_status check_mode(infft_plan_t p, int mode) {
+}  // extern "C"
+
+namespace infft {
+
+infft_status check_mode(const infft_plan_s* p, int mode) {
     if (mode == INFFT_MODE_DCF && !p->has_weights) { set_error("DCF mode needs weights"); return INFFT_ESTATE; }
     if (mode == INFFT_MODE_BOPT && !p->has_bopt) { set_error("BOPT mode needs infft_optimize_B"); return INFFT_ESTATE; }
     if (mode < 0 || mode > 2) { set_error("bad mode %d", mode); return INFFT_EINVAL; }
@@ -604,6 +609,10 @@ static infft_status check_mode(infft_plan_t p, int mode) {
     }
     return INFFT_OK;
 }
+
+}  // namespace infft
+
+extern "C" {
 
 static size_t coeff_count(const infft_plan_s* p) {
     size_t k = 1;

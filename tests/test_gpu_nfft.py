@@ -265,14 +265,17 @@ def test_fp32_d2_other_m_match_oracle_algorithm(m, gen):
     assert rel(h, NF.adjoint_nfft(x, f, M, sigma, m)) < 1e-5
 
 
-@pytest.mark.parametrize("N", [1, 2, 3, 33])
+@pytest.mark.parametrize("N", [1, 2, 3, 31, 32, 33, 65])
 def test_fp32_d2_tiny_point_counts(N):
-    """Work items of one to 33 points (a lone point leaves the second half-warp idle) give the
-    oracle's Algorithm 2.4 to float32 rounding."""
+    """One work item of one to 65 points (a lone point leaves the second half-warp idle;
+    33 and 65 points cross the 32-point staging and prefetch chunks by one) gives the
+    oracle's Algorithm 2.4 to float32 rounding.  M = 8 makes the oversampled grid a single
+    16 x 16 tile, so all points form one item."""
     L, torch = lib_or_skip()
-    M, sigma, m = 16, 2.0, 4
+    M, sigma, m = 8, 2.0, 3
     x = inputs.random_points(N, 2, 43 + N)
     f = inputs.samples_complex(N, 44 + N)
     p = L.Plan(x, M, sigma, m, "fp32")
+    assert p.work_items == 1
     h = p.adjoint(to_dev(torch, f, torch.complex64)).cpu().numpy()
     assert rel(h, NF.adjoint_nfft(x, f, M, sigma, m)) < 1e-5
