@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--cg-iters", type=int, default=25)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-bopt", action="store_true", help="C3: skip the B_opt leg (Algorithms 4.3 / 4.4)")
+    ap.add_argument("--no-tune", action="store_true", help="C3: the library's default kernel choices")
+    ap.add_argument("--retune", action="store_true", help="C3: search the kernel choices even if cached")
     ap.add_argument("--t51-max", type=int, default=1024, help="T51: largest M of the linogram sweep")
     ap.add_argument("--t51-bopt-max", type=int, default=32, help="T51: largest M with B_opt (Algorithm 4.3)")
     ap.add_argument("--config", default="C3", choices=["C1", "C2", "C3", "C4", "C5", "T51"],
@@ -62,18 +65,14 @@ def parse():
     ap.add_argument("--rate", type=float, default=500.0, help="C5: mean arrival rate (requests/s)")
     ap.add_argument("--requests", type=int, default=20000, help="C5: number of requests")
     ap.add_argument("--new-frac", type=float, default=0.2, help="C5: fraction of requests on new point sets")
+    ap.add_argument("--bopt-on-admit", action="store_true",
+                    help="C5: also optimise B (Algorithm 4.3) on admit and serve with B_opt (Algorithm 4.4)")
     ap.add_argument("--time-limit", type=float, default=120.0, help="C5: wall-clock cap of the serving run (s)")
     return ap.parse_args()
 
 
 # --------------------------------------------------------------------------------------
 # oracle on the host (cpu_baseline / reference arm)
-
-def _oracle_chunk(args):
-    x, f, M, ks = args
-    from oracle import fourier as FO
-    return FO.adjoint_ndft(x, f, M, k_subset=ks)
-
 
 def _oracle_parity(args):
     """The oracle's exact sums for a parity sample, in blocks of about 16M exponentials so
@@ -83,31 +82,45 @@ def _oracle_parity(args):
     return FO.adjoint_ndft(x, f, M, k_subset=ks, chunk=max(1, min(256, (1 << 24) // max(1, x.shape[0]))))
 
 
-def oracle_cost(x, f, M, seconds, pool, cores, seed=0):
-    """Time the oracle's exact adjoint sums (eq. nfft*) for a bounded random subset of
-    I_M: one calibration chunk, then one chunk sized to fill about `seconds`.  Returns
-    (seconds per point and coefficient, description of the sample)."""
-    K = M * M
+def _oracle_recon(args):
+    """One complete reconstruction by the oracle: its float64 Algorithm 2.4 applied to W f
+    (Algorithm 3.7), KB m=4, sigma=2.  Returns the seconds it took in this worker."""
+    M, x, seed = args
+    import inputs
+    from oracle import nfft as NF
     N = x.shape[0]
-    rng = np.random.default_rng(seed)
-
-    def run(n):
-        ks = rng.choice(K, size=min(n, K), replace=False)
-        chunks = [(x, f, M, c) for c in np.array_split(ks, cores) if len(c)]
-        t0 = time.perf_counter()
-        pool.map(_oracle_chunk, chunks)
-        return time.perf_counter() - t0, len(ks)
-
-    t1, n1 = run(cores)
-    n2 = int(max(0.0, seconds - t1) / (t1 / n1))
-    t2, n2 = run(n2) if n2 > 0 else (0.0, 0)
-    cost = (t1 + t2) / ((n1 + n2) * N)
-    return cost, f"{n1 + n2} of {K} coefficients of one M={M}, N={N} set (exact sums), extrapolated by N*M^2"
+    c = inputs.samples_complex(N, seed) / N      # W f with w_j = 1/N (any weights cost the same)
+    t0 = time.perf_counter()
+    NF.adjoint_nfft(x, c, M, 2.0, 4)
+    return time.perf_counter() - t0
 
 
-def batch_rate_from_cost(cost, sets):
-    """Reconstructions per second of the whole batch at `cost` seconds per point-coefficient."""
-    return len(sets) / sum(cost * x.shape[0] * M * M for M, x in sets)
+def oracle_sample(sets, step: int, per_m: int):
+    """Complete sets for one oracle step: `per_m` sets of every degree M of the batch,
+    taken in turn (step k takes the k-th group), so that the sample keeps the batch's
+    even mix of M."""
+    by_m = {}
+    for i, (M, x) in enumerate(sets):
+        by_m.setdefault(M, []).append(i)
+    pick = []
+    for M in sorted(by_m):
+        idx = by_m[M]
+        for r in range(per_m):
+            pick.append(idx[(step * per_m + r) % len(idx)])
+    return pick
+
+
+def oracle_step(sets, pick, pool):
+    """Run the oracle on the picked complete sets in the pool; wall seconds of the step."""
+    t0 = time.perf_counter()
+    pool.map(_oracle_recon, [(sets[i][0], sets[i][1], 1000 + i) for i in pick], chunksize=1)
+    return time.perf_counter() - t0
+
+
+def oracle_sample_text(sets, pick, cores):
+    Ms = sorted({sets[i][0] for i in pick})
+    return (f"{len(pick)} complete sets per step ({len(pick) // max(1, len(Ms))} of each M in {Ms}) of the "
+            f"64-set batch, the oracle's float64 Algorithm 2.4 applied to W f, {cores} worker processes")
 
 
 # --------------------------------------------------------------------------------------
@@ -217,39 +230,106 @@ def measured_peak():
 
 # --------------------------------------------------------------------------------------
 
+def bench_config(sets, world, **extra):
+    """The config object of the batched workload (both arms)."""
+    cfg = {"workload": WORKLOAD, "sets": len(sets), "d": 2, "M": sorted({M for M, _ in sets}),
+           "N_total": int(sum(x.shape[0] for _, x in sets)), "m": 4, "sigma": 2.0, "mode": "DCF",
+           "l2": "no flush: per-step inputs (points, weights, samples, scratch) exceed the 129 MB L2",
+           "parallelism": f"replicas x{world}"}
+    cfg.update(extra)
+    return cfg
+
+
 def run_reference(args, rank, world):
+    """The reference arm: the oracle on the host cores.  Each step reconstructs a stratified
+    sample of complete sets of the batch (four of every M) with the oracle's float64
+    Algorithm 2.4; the step time is the measured wall time of that sample."""
     import inputs
     if rank != 0:
         return
     cores = len(os.sched_getaffinity(0))
     sets = inputs.batch_sets(args.sets, args.seed)
-    M, x = max(sets, key=lambda s: s[0] * 10 ** 9 + s[1].shape[0])
-    f = inputs.samples_complex(x.shape[0], 1)
     ctx = mp.get_context("spawn")
     os.environ["OPENBLAS_NUM_THREADS"] = "1"
     os.environ["OMP_NUM_THREADS"] = "1"
-    per_step = min(10.0, 150.0 / max(1, args.steps + args.warmup))   # the whole run: about 150 s
+    per_m = 4
     with ctx.Pool(cores) as pool:
         for k in range(args.warmup):
-            oracle_cost(x, f, M, per_step / 4, pool, cores, seed=k)
-        rates = []
-        t0 = time.perf_counter()
+            oracle_step(sets, oracle_sample(sets, k, per_m), pool)
+        step_s, n_recon = [], 0
         for k in range(args.steps):
-            cost, sample = oracle_cost(x, f, M, per_step, pool, cores, seed=100 + k)
-            rates.append(batch_rate_from_cost(cost, sets))
-        wall = time.perf_counter() - t0
-    value = statistics.median(rates)
+            pick = oracle_sample(sets, args.warmup + k, per_m)
+            step_s.append(oracle_step(sets, pick, pool))
+            n_recon += len(pick)
+    total = sum(step_s)
+    value = n_recon / total
+    sample = oracle_sample_text(sets, pick, cores)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "recon/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * len(sets) / value, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD + "; reference = FP64 exact sums (oracle) on the host",
-                       "sample_set": {"M": M, "N": int(x.shape[0])},
-                       "note": "each step times a bounded sample of one M=256 set and extrapolates the "
-                               "whole 64-set batch by N_i*M_i^2"},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": bench_config(sets, world),
+            "p50_ms": 1e3 * statistics.median(step_s), "p99_ms": 1e3 * float(np.percentile(step_s, 99)),
+            "recon_per_step": n_recon // args.steps,
             "cpu_baseline": {"value": value, "unit": "recon/s", "cores": cores, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": "recon/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "wall_s": wall}
+            "e2e": {"value": value, "unit": "recon/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def bopt_leg(L, torch, sets, dev, peak, peak_kind, rank):
+    """Algorithm 4.3 (B_opt, float64 least squares, 2m+2 slots, KB window) on 16 complete
+    sets of the batch (four of every M), then the reconstruction of Algorithm 4.4 on them as
+    one graph replay.  Reports the precompute rate, the reconstruction rate, the event-timed
+    B_opt spread and its HBM roofline: the spread streams (2m+2)^2 complex64 coefficients
+    per point, N (4d + 8 + 8 P) + 8 G bytes per launch (P = (2m+2)^d)."""
+    import inputs
+    pick = oracle_sample(sets, 0, 4)
+    sub = [sets[i] for i in pick]
+    plans, fs, hs, res = [], [], [], []
+    t0 = time.perf_counter()
+    for k, (M, x) in enumerate(sub):
+        p = L.Plan(x, M, 2.0, 4, "fp32")
+        res.append(p.optimize_B())
+        plans.append(p)
+        fs.append(torch.from_numpy(inputs.samples_complex(x.shape[0], 3000 + k).astype(np.complex64)).to(dev))
+        hs.append(torch.empty((M, M), dtype=torch.complex64, device=dev))
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    batch = L.Batch(plans, fs, hs, L.MODE_BOPT)
+    for _ in range(3):
+        batch.run()
+    torch.cuda.synchronize()
+    steps = 20
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        batch.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    stage = [L.adjoint_batched_timed(plans, fs, hs, L.MODE_BOPT) for _ in range(5)]
+    spread_ms = statistics.median(st["spread"] for st in stage)
+    Ntot = sum(x.shape[0] for _, x in sub)
+    G = sum(p.Ms ** 2 for p in plans)
+    Pt = (2 * 4 + 2) ** 2
+    nbytes = Ntot * (4 * 2 + 8 + 8 * Pt) + 8 * G
+    achieved = nbytes / (spread_ms / 1e3) / 1e9
+    err = None
+    if rank == 0:   # one M=64 set against the oracle's Algorithm 4.4 with the library's own B_opt
+        from oracle import bopt as BO
+        i64 = next(k for k, (M, _) in enumerate(sub) if M == 64)
+        M, x = sub[i64]
+        ref = BO.reconstruct(x, fs[i64].cpu().numpy().astype(np.complex128), plans[i64].get_bopt(), M, 2.0, 4,
+                             "kb", BO.PATTERN_2M2)
+        got = hs[i64].cpu().numpy().ravel()
+        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    return {"sets": len(sub), "M": sorted({M for M, _ in sub}), "N_total": int(Ntot),
+            "precompute_s": build_s, "builds_per_s": len(sub) / build_s, "max_col_residual": max(res),
+            "recon_per_s": len(sub) / (ms / 1e3), "ms_per_step": ms, "spread_ms": spread_ms,
+            "rel_err_vs_fp64_alg44": err,
+            "roofline": {"bound": "hbm", "kernel": "k_spread2d (B_opt)", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+                         "algorithmic_bytes": int(nbytes)}}
 
 
 def run_ours(args, rank, world, dist):
@@ -270,21 +350,27 @@ def run_ours(args, rank, world, dist):
 
     # ---- set-up (untimed): plans, weights, buffers -------------------------------------
     sets = inputs.batch_sets(args.sets, args.seed + 7919 * rank)
+    fs = [torch.from_numpy(inputs.samples_complex(x.shape[0], 1000 + i).astype(np.complex64)).to(dev)
+          for i, (M, x) in enumerate(sets)]
+    # kernel choices for this workload: the autotuner's cached result, or a fresh search
+    tuning = None
+    if not args.no_tune:
+        from paper_2302_00414_gb300 import tune as TU
+        tuning = TU.tuned_choice(L, torch, sets, fs, 4, "fp32", L.MODE_DCF, retune=args.retune)
+    tune_cfg = tuning["tune"] if tuning else None
     t_setup = time.perf_counter()
-    plans, fs, hs, wres = [], [], [], []
+    plans, hs, wres = [], [], []
     t_plan = t_w = 0.0
     for i, (M, x) in enumerate(sets):
         t0 = time.perf_counter()
-        p = L.Plan(x, M, 2.0, 4, "fp32")
+        p = L.Plan(x, M, 2.0, 4, "fp32", tune=tune_cfg)
         torch.cuda.synchronize()
         t_plan += time.perf_counter() - t0
         t0 = time.perf_counter()
         info = p.weights(max_iter=args.cg_iters, rel_tol=1e-12)
         t_w += time.perf_counter() - t0
         wres.append(info["residual_inf"])
-        f = torch.from_numpy(inputs.samples_complex(x.shape[0], 1000 + i).astype(np.complex64)).to(dev)
         plans.append(p)
-        fs.append(f)
         hs.append(torch.empty((M, M), dtype=torch.complex64, device=dev))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_setup
@@ -347,18 +433,32 @@ def run_ours(args, rank, world, dist):
     plain_rate = plain_rounds * len(plans) / plain_s
 
     # ---- end to end through the C ABI with pinned host buffers ---------------------------
+    # (the graph of one step over page-locked host buffers: every replay copies the step's
+    # samples in and its coefficients out; and the same through the per-call API)
     f_host = [f.cpu().pin_memory() for f in fs]
     h_host = [torch.empty(h.shape, dtype=h.dtype).pin_memory() for h in hs]
     fh_np = [t.numpy() for t in f_host]
     hh_np = [t.numpy() for t in h_host]
+    hbatch = L.Batch(plans, fh_np, hh_np, L.MODE_DCF)
+    for _ in range(3):
+        hbatch.run()
+    torch.cuda.synchronize()
+    e2e_times = []
+    for _ in range(max(5, min(args.steps, 50))):
+        t0 = time.perf_counter()
+        hbatch.run()
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_rate = world * len(plans) / statistics.median(e2e_times)
+    hbatch.close()
     for _ in range(2):
         L.adjoint_batched(plans, fh_np, hh_np, L.MODE_DCF)
-    e2e_times = []
+    call_times = []
     for _ in range(max(3, min(args.steps, 10))):
         t0 = time.perf_counter()
         L.adjoint_batched(plans, fh_np, hh_np, L.MODE_DCF)
-        e2e_times.append(time.perf_counter() - t0)
-    e2e_rate = world * len(plans) / statistics.median(e2e_times)
+        call_times.append(time.perf_counter() - t0)
+    e2e_call_rate = world * len(plans) / statistics.median(call_times)
     h2d = sum(int(f.numel()) * 8 for f in fs)
     d2h = sum(int(h.numel()) * 8 for h in hs)
 
@@ -379,18 +479,22 @@ def run_ours(args, rank, world, dist):
             got = hs[i].cpu().numpy().ravel()[ks]
             rel_errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
 
-    # ---- CPU baseline: the oracle on a bounded sample --------------------------------------
+    # ---- B_opt leg: Algorithm 4.3 on a stratified sample of the sets, then Algorithm 4.4 --
+    bopt = None
+    if not args.no_bopt:
+        bopt = bopt_leg(L, torch, sets, dev, peak, peak_kind, rank)
+
+    # ---- CPU baseline: the oracle on complete sets (one reference step) -------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = len(os.sched_getaffinity(0))
-        M, x = max(sets, key=lambda s: s[0] * 10 ** 9 + s[1].shape[0])
-        f = inputs.samples_complex(x.shape[0], 1)
         os.environ["OPENBLAS_NUM_THREADS"] = "1"
         os.environ["OMP_NUM_THREADS"] = "1"
+        pick = oracle_sample(sets, 0, 4)
         with mp.get_context("spawn").Pool(cores) as pool:
-            cost, sample = oracle_cost(x, f, M, args.cpu_seconds, pool, cores)
-        cpu = {"value": batch_rate_from_cost(cost, sets), "unit": "recon/s", "cores": cores, "kind": "oracle",
-               "sample": sample}
+            wall = oracle_step(sets, pick, pool)
+        cpu = {"value": len(pick) / wall, "unit": "recon/s", "cores": cores, "kind": "oracle",
+               "sample": oracle_sample_text(sets, pick, cores), "seconds": wall}
 
     if rank != 0:
         return
@@ -399,10 +503,7 @@ def run_ours(args, rank, world, dist):
         "metric": METRIC, "value": recon_per_s, "unit": "recon/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sets": len(plans), "d": 2, "M": sorted({M for M, _ in sets}),
-                   "N_total": int(Ntot), "m": 4, "sigma": 2.0, "mode": "DCF",
-                   "l2": "no flush: per-step inputs (points, weights, samples, scratch) exceed the 129 MB L2",
-                   "parallelism": f"replicas x{world}"},
+        "config": bench_config(sets, world),
         "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
         "plain": {"value": plain_rate, "unit": "recon/s"}, "vs_plain": recon_per_s / world / plain_rate,
         "rel_err_vs_fp64": max(rel_errs) if rel_errs else None,
@@ -411,12 +512,17 @@ def run_ours(args, rank, world, dist):
                      "unit": "GB/s", "frac": achieved / peak, "traffic": profiled_traffic(),
                      "peak_kind": peak_kind, "algorithmic_bytes": int(spread_bytes),
                      "note": "bound on chip (ncu: shared-memory wavefronts 71% of peak, issue 59%, DRAM 9%), see profiles/"},
-        "e2e": {"value": e2e_rate, "unit": "recon/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_rate, "unit": "recon/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "path": "graph replay over page-locked host buffers (infft_batch_create / infft_batch_run)"},
+        "e2e_call": {"value": e2e_call_rate, "unit": "recon/s",
+                     "path": "infft_adjoint_batched with page-locked host buffers, one call per step"},
         "gpu_launches": int(kernels_per_step * args.steps),
         "clocks": clocks,
         "precompute": {"setup_s": setup_s, "plan_s": t_plan, "weights_s": t_w, "cg_iters": args.cg_iters,
                        "weights_residual_max": max(wres)},
         "cpu_baseline": cpu,
+        "bopt": bopt,
+        "tuning": tuning,
     }
     print(json.dumps(line), flush=True)
 
@@ -619,7 +725,7 @@ def run_serving(args, rank, world, dist):
     torch.cuda.set_device(dev)
     rng = np.random.default_rng(5000 + rank)
     cg_iters = min(args.cg_iters, 10)
-    be = Backend(weights_iters=cg_iters)
+    be = Backend(weights_iters=cg_iters, bopt=args.bopt_on_admit)
     budget = int(0.5 * torch.cuda.mem_get_info()[0])
     kept = {}
 

@@ -124,6 +124,37 @@ infft_status infft_plan(int d, int M, int64_t N, const double* x, double sigma, 
                         unsigned flags, void* stream, infft_plan_t* out);
 
 /*
+ * Tuning of a plan's kernels: the choices the library otherwise makes by itself.  The paper
+ * has no counterpart; the values change speed only, never results beyond the rounding of
+ * a different summation order (the spread tile and the item cap change which padded tiles
+ * hold a point's taps, the others the schedule).  0 in a field keeps the library's default.
+ *   tile      : edge T of the spreading tiles (a power of two, m < T <= M_sigma; the register-row
+ *               spread of d = 2 needs T + 2m + 1 <= 32 and the fused merge-FFT kernel T in
+ *               {8, 16}); default 16 for d = 2, 8 for d = 3, min(256, M_sigma) for d = 1.
+ *   item_cap  : most points per work item, >= 1 (default 512; 32 for d = 1).
+ *   branches  : concurrent branches of batched adjoints whose first plan is this one (1..8;
+ *               default 3 with device buffers, 8 with host buffers).
+ *   prefetch  : spreading kernels copy the next points' data to shared memory while they
+ *               spread the current ones: 1 on, 2 off (default: by form and grid size).
+ *   fused_fft : d = 2 adjoints merge the padded tiles and run both FFT passes in one
+ *               thread-block-cluster kernel: 1 on (where the grid fits), 2 off (default off).
+ * An environment variable (INFFT_SPREAD2D_PREFETCH, INFFT_SPREAD3D_PREFETCH,
+ * INFFT_FUSED_MERGE_FFT, INFFT_BATCH_BRANCHES) applies only where the plan leaves the field 0.
+ */
+typedef struct {
+    int tile;
+    int item_cap;
+    int branches;
+    int prefetch;
+    int fused_fft;
+} infft_tune_t;
+
+/* infft_plan_tuned -- infft_plan with tuning (tune may be NULL: all defaults).  Invalid
+ * tuning values give INFFT_EINVAL. */
+infft_status infft_plan_tuned(int d, int M, int64_t N, const double* x, double sigma, int m,
+                              unsigned flags, const infft_tune_t* tune, void* stream, infft_plan_t* out);
+
+/*
  * infft_weights -- Algorithm 3.6: density compensation weights for exact
  * reconstruction (Corollary 3.4, eq. claim_quadrature_coefficients_double).
  * If (2M)^d <= N: CG on A_2M^* A_2M u = e_0 (the normal equations of the
@@ -134,7 +165,11 @@ infft_status infft_plan(int d, int M, int64_t N, const double* x, double sigma, 
  * truncation m_cg (<= 0 selects 8 for d <= 2 and 4 for d = 3), or, in the second
  * kind, the convolution form of infft_weights_opts below; CG vectors,
  * inner products and updates are float64.  x0 = 0, stop when
- * ||r||_2 / ||b||_2 <= rel_tol or after max_iter iterations.
+ * ||r||_2 / ||b||_2 <= rel_tol or after max_iter iterations.  The CG state stays on the
+ * device: the host looks at it once per eight queued iterations, and iterations queued after
+ * the stop do nothing.  The weights come from the CG iterate (x_1, x_2, ...) of smallest
+ * ||r||_2, so that a capped run returns the best weights it met: in the second kind ||r||_2
+ * is exactly the 2-norm of A_2M^T w - e_0, which therefore does not grow with max_iter.
  *   residual_inf : (out, may be NULL) max_k |[A_2M^T w]_k - delta_{0,k}| over
  *                  I_2M, evaluated with the same float64 NFFT.
  *   iters        : (out, may be NULL) CG iterations taken.
@@ -206,6 +241,31 @@ infft_status infft_get_bopt(infft_plan_t plan, void* coeff, void* stream);
  */
 infft_status infft_adjoint(infft_plan_t plan, int mode, const void* f, void* fhat, void* stream);
 
+/*
+ * The steps of the adjoint NFFT (Algorithm 2.4) one at a time, for callers that place a
+ * collective between them -- the point-sharded adjoint over several GPUs, where every rank
+ * spreads its own points into a whole grid, the grids are summed with a reduce-scatter of
+ * slabs, and the pruned FFT runs on slabs with one all-to-all between the axes.
+ *
+ * infft_spread_grid -- step 1 of Algorithm 2.4 (with W for INFFT_MODE_DCF, B_opt^* for
+ * INFFT_MODE_BOPT): g_l = sum_j c_j w~_m(x_j - l/M_sigma) for every l of the oversampled
+ * grid.  f: N complex (device), the caller's point order.  grid: M_sigma^d complex (device),
+ * C order, l stored at l mod M_sigma along every axis.  Uses the plan's scratch set 0 (as
+ * infft_adjoint).  Stream ordered.
+ *
+ * infft_fft_axis -- steps 2 and 3 of Algorithm 2.4 along one axis: for an input tensor
+ * in[a][l][b] (A x M_sigma x B, device, complex), out[a][i][b] = (1/(M_sigma w^(k))) sum_l
+ * in[a][l][b] exp(-2 pi i k l / M_sigma), k = i - M/2, i = 0..M-1 (the crop to I_M and
+ * the deconvolution of eq. matrix_D of that axis; mode picks the window of D as in
+ * infft_adjoint).  The output is written as nblk blocks along i (nblk divides M): block c
+ * holds the (A x M/nblk x B) tensor of i = c M/nblk .. (c+1) M/nblk - 1, contiguous, so that
+ * block c can be sent to rank c of an all-to-all as it is (nblk = 1: the plain A x M x B
+ * tensor).  Stream ordered.
+ */
+infft_status infft_spread_grid(infft_plan_t plan, int mode, const void* f, void* grid, void* stream);
+infft_status infft_fft_axis(infft_plan_t plan, int mode, int64_t A, int64_t B, int nblk, const void* in, void* out,
+                            void* stream);
+
 /* infft_forward -- Algorithm 2.1, f ~ A fhat (fhat: M^d complex, f: N complex). */
 infft_status infft_forward(infft_plan_t plan, const void* fhat, void* f, void* stream);
 
@@ -266,10 +326,14 @@ infft_status infft_adjoint_batched_timed(const infft_plan_t* plans, int count, i
 
 /*
  * Graph-replayed batches.  infft_batch_create records the batched adjoint for
- * fixed plans and fixed device buffers f[i] / fhat[i] into a CUDA graph;
+ * fixed plans and fixed buffers f[i] / fhat[i] into a CUDA graph;
  * infft_batch_run replays it on `stream`.  The plans and buffers must outlive
- * the batch, and the buffers must be device memory.  The graph holds the jobs in the
- * concurrent branches of infft_adjoint_batched.  Plans may repeat as in
+ * the batch.  The buffers are device memory or page-locked host memory (cudaHostAlloc,
+ * cudaHostRegister; pageable memory gives INFFT_EINVAL): for host buffers the graph also
+ * holds the copies to and from the plans' I/O buffers, so one replay moves a whole step's
+ * inputs and results, and the caller synchronises `stream` before reading fhat.  A plan with
+ * host buffers may appear only once.  The graph holds the jobs in the concurrent branches of
+ * infft_adjoint_batched (eight with host buffers).  Plans may repeat as in
  * infft_adjoint_batched; the extra scratch grids are allocated before the capture starts.
  */
 infft_status infft_batch_create(const infft_plan_t* plans, int count, int mode,

@@ -38,6 +38,8 @@ _lib = None
 _SIGS = {
     "infft_plan": (C.c_int, [C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_double, C.c_int, C.c_uint, C.c_void_p,
                              C.POINTER(C.c_void_p)]),
+    "infft_plan_tuned": (C.c_int, [C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_double, C.c_int, C.c_uint,
+                                   C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
     "infft_weights": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double),
                                 C.POINTER(C.c_int), C.c_void_p]),
     "infft_weights_opts": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_uint, C.POINTER(C.c_double),
@@ -60,6 +62,9 @@ _SIGS = {
                                      C.POINTER(C.c_void_p), C.c_void_p, C.POINTER(C.c_void_p)]),
     "infft_batch_run": (C.c_int, [C.c_void_p, C.c_void_p]),
     "infft_adjoint_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "infft_spread_grid": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "infft_fft_axis": (C.c_int, [C.c_void_p, C.c_int, C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_void_p,
+                                 C.c_void_p]),
     "infft_batch_destroy": (None, [C.c_void_p]),
     "infft_plan_N": (C.c_int64, [C.c_void_p]),
     "infft_plan_Msigma": (C.c_int, [C.c_void_p]),
@@ -116,9 +121,31 @@ def launch_count_reset():
 
 # ---- raw entry points, same names as the C ABI (integer pointers) ----------------------
 
+class Tune(C.Structure):
+    """infft_tune_t: the plan's kernel choices (0 = the library's default)."""
+    _fields_ = [("tile", C.c_int), ("item_cap", C.c_int), ("branches", C.c_int), ("prefetch", C.c_int),
+                ("fused_fft", C.c_int)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+TUNE_FIELDS = tuple(k for k, _ in Tune._fields_)
+
+
 def infft_plan(d, M, N, x_ptr, sigma, m, flags, stream=0):
     out = C.c_void_p()
     return load().infft_plan(d, M, N, x_ptr, sigma, m, flags, stream, C.byref(out)), out.value
+
+
+def infft_plan_tuned(d, M, N, x_ptr, sigma, m, flags, tune=None, stream=0):
+    """tune: a dict with keys of TUNE_FIELDS (missing keys 0), or None."""
+    out = C.c_void_p()
+    t = None
+    if tune:
+        t = Tune(**{k: int(tune.get(k, 0)) for k in TUNE_FIELDS})
+    return load().infft_plan_tuned(d, M, N, x_ptr, sigma, m, flags, C.byref(t) if t is not None else None, stream,
+                                   C.byref(out)), out.value
 
 
 def infft_weights(plan, max_iter, rel_tol, m_cg=0, stream=0, opts=0):
@@ -145,6 +172,16 @@ def infft_adjoint_noalloc(plan, mode, f_ptr, fhat_ptr, stream=0):
     """The reconstruction of infft_adjoint with the per-call scratch in the library's
     fixed device array (device pointers only; see include/infft.h)."""
     return load().infft_adjoint_noalloc(plan, mode, f_ptr, fhat_ptr, stream)
+
+
+def infft_spread_grid(plan, mode, f_ptr, grid_ptr, stream=0):
+    """Step 1 of Algorithm 2.4 into a caller's M_sigma^d grid (device pointers)."""
+    return load().infft_spread_grid(plan, mode, f_ptr, grid_ptr, stream)
+
+
+def infft_fft_axis(plan, mode, A, B, nblk, in_ptr, out_ptr, stream=0):
+    """Steps 2-3 of Algorithm 2.4 along the middle axis of an (A, M_sigma, B) tensor."""
+    return load().infft_fft_axis(plan, mode, A, B, nblk, in_ptr, out_ptr, stream)
 
 
 def infft_forward(plan, fhat_ptr, f_ptr, stream=0):
@@ -201,8 +238,10 @@ class Plan:
     """A plan for fixed points x (N x d, float64 numpy array or torch tensor)."""
 
     def __init__(self, x, M: int, sigma: float = 2.0, m: int = 4, precision: str = "fp32",
-                 window: str = "kb", stream=None, pooled: bool = False):
+                 window: str = "kb", stream=None, pooled: bool = False, tune=None):
+        """tune: optional dict of kernel choices (see infft_tune_t in include/infft.h)."""
         self.precision, self.window = precision, window
+        self.tune = dict(tune) if tune else None
         self.has_weights = self.has_bopt = False
         flags = {"fp32": FP32, "fp64": FP64}[precision] | (POOLED if pooled else 0)
         flags |= {"kb": WIN_KB, "bspline": WIN_BSPLINE, "dirichlet": WIN_DIRICHLET}[window]
@@ -219,7 +258,11 @@ class Plan:
                 x = x[:, None]
             N, d = x.shape
         self.d, self.M, self.N, self.m, self.sigma = int(d), int(M), int(N), int(m), float(sigma)
-        s, h = infft_plan(self.d, self.M, self.N, _ptr(x), self.sigma, self.m, flags, _stream(stream))
+        if self.tune:
+            s, h = infft_plan_tuned(self.d, self.M, self.N, _ptr(x), self.sigma, self.m, flags, self.tune,
+                                    _stream(stream))
+        else:
+            s, h = infft_plan(self.d, self.M, self.N, _ptr(x), self.sigma, self.m, flags, _stream(stream))
         _check(s)
         self.handle = h
         self.Ms = int(load().infft_plan_Msigma(h))
@@ -260,6 +303,17 @@ class Plan:
         return {"status": s, "residual_inf": res, "iters": it}
 
     def set_weights(self, w, stream=None):
+        """N weights in the caller's point order: any numpy array (converted to complex128)
+        or a complex128 torch tensor."""
+        if isinstance(w, np.ndarray):
+            w = np.ascontiguousarray(w, dtype=np.complex128).ravel()
+            if w.size != self.N:
+                raise ValueError(f"{w.size} weights for {self.N} points")
+        else:
+            import torch
+            if w.dtype != torch.complex128 or w.numel() != self.N:
+                raise ValueError("weights must be a complex128 tensor of N entries")
+            w = w.contiguous()
         _check(load().infft_set_weights(self.handle, _ptr(w), _stream(stream)))
         self.has_weights = True
 
@@ -341,7 +395,9 @@ def adjoint_batched_timed(plans, fs, fhats, mode: int = MODE_PLAIN, stream=None)
 
 
 class Batch:
-    """A CUDA graph of the batched adjoint over fixed plans and fixed device buffers."""
+    """A CUDA graph of the batched adjoint over fixed plans and fixed buffers: device tensors,
+    or page-locked host arrays (numpy views of pinned torch tensors), whose copies the graph
+    then holds; after run() synchronise the stream before reading host results."""
 
     def __init__(self, plans, fs, fhats, mode: int = MODE_PLAIN, stream=None):
         n = len(plans)

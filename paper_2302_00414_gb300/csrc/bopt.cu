@@ -129,19 +129,45 @@ __host__ __device__ __forceinline__ long long tri(long long r, long long c) { re
 
 constexpr int BOPT_THREADS = 256;
 
-// Persistent solver: each block takes columns in turn.  G_l lives in shared memory
-// when n(n+1)/2 entries fit, otherwise in the block's slice of `gscratch`.
+// bytes of the per-column arrays (v, y, current column of L, member points, member ids),
+// rounded up to 256 so that consecutive per-block slices keep the 16-byte complex arrays aligned
+__host__ __device__ __forceinline__ size_t bopt_fixed_bytes(int n, int d) {
+    return ((size_t)n * (16 * 3 + 8 * d + 8) + 255) & ~(size_t)255;
+}
+
+// (row, column) of entry e of a packed lower triangle (e = r (r + 1) / 2 + c, c <= r): a
+// float estimate of the row, corrected by integer steps
+__device__ __forceinline__ void tri_rc(long long e, long long* r_out, long long* c_out) {
+    long long r = (long long)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+    while (r * (r + 1) / 2 > e) --r;
+    while ((r + 1) * (r + 2) / 2 <= e) ++r;
+    *r_out = r;
+    *c_out = e - r * (r + 1) / 2;
+}
+
+// Persistent solver over a list of columns: each block takes the next column of `list`
+// from the counter `next`, so blocks that drew large columns do not hold up the others
+// (every column's arithmetic is independent of the block that solves it).  G_l lives in
+// shared memory when n(n+1)/2 entries fit (n <= n_smem), otherwise in the block's slice
+// of `gscratch` (n_max = the largest column of the list).  The per-column
+// arrays live in shared memory when the largest column's fit (fix_smem), otherwise in the
+// block's slice of `gfix` (columns of thousands of members: the centre of a linogram grid).
 __global__ void __launch_bounds__(BOPT_THREADS) k_bopt_solve(BoptGeom g, const int* __restrict__ start,
                                                              const long long* __restrict__ members,
                                                              const double* __restrict__ x64,
                                                              const cx<double>* __restrict__ V, double rhs2,
-                                                             int n_smem, int n_max, cx<double>* __restrict__ gscratch,
+                                                             const int* __restrict__ list, int nlist,
+                                                             int* __restrict__ next, int n_smem, int n_max,
+                                                             cx<double>* __restrict__ gscratch,
+                                                             int fix_smem, unsigned char* __restrict__ gfix,
                                                              cx<double>* __restrict__ coef, double* __restrict__ eps,
                                                              int* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // 16-byte aligned complex arrays first, then the 8-byte arrays
     cx<double>* Gs = reinterpret_cast<cx<double>*>(smem_raw);     // packed lower, tri(n_smem + 1)
-    cx<double>* vv = Gs + tri(n_smem + 1, 0);                      // n_max: right side v_l
+    unsigned char* fix = fix_smem ? reinterpret_cast<unsigned char*>(Gs + tri(n_smem + 1, 0))
+                                  : gfix + (size_t)blockIdx.x * bopt_fixed_bytes(n_max, g.d);
+    cx<double>* vv = reinterpret_cast<cx<double>*>(fix);          // n_max: right side v_l
     cx<double>* yy = vv + n_max;                                  // n_max: solution in place
     cx<double>* colk = yy + n_max;                                // n_max: current column of L
     double* xs = reinterpret_cast<double*>(colk + n_max);         // n_max * d
@@ -150,9 +176,15 @@ __global__ void __launch_bounds__(BOPT_THREADS) k_bopt_solve(BoptGeom g, const i
     __shared__ int s_fail;
     __shared__ double s_trace;
     const int tid = threadIdx.x, nth = blockDim.x;
-    const long long ncols = (long long)ipow(g.Ms, g.d);
+    __shared__ int s_item;
 
-    for (long long col = blockIdx.x; col < ncols; col += gridDim.x) {
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(next, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();   // every thread has read s_item before thread 0 draws again
+        if (item >= nlist) break;
+        const long long col = list[item];
         const int a = start[col];
         const int n = start[col + 1] - a;
         if (n == 0) {
@@ -181,11 +213,8 @@ __global__ void __launch_bounds__(BOPT_THREADS) k_bopt_solve(BoptGeom g, const i
             // G_l (lower triangle) from the Dirichlet closed form, plus the diagonal shift
             const long long ne = tri(n, 0);
             for (long long e = tid; e < ne; e += nth) {
-                const long long r = (long long)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
-                long long rr = r;
-                while (tri(rr + 1, 0) <= e) ++rr;
-                while (tri(rr, 0) > e) --rr;
-                const long long c = e - tri(rr, 0);
+                long long rr, c;
+                tri_rc(e, &rr, &c);
                 cx<double> v = mk<double>(1.0, 0.0);
                 for (int t = 0; t < g.d; ++t) v = mul(v, gram_factor(xs[rr * g.d + t] - xs[c * g.d + t], g.M));
                 if (g.real_field) v.im = 0.0;
@@ -222,11 +251,11 @@ __global__ void __launch_bounds__(BOPT_THREADS) k_bopt_solve(BoptGeom g, const i
                 }
                 __syncthreads();
                 const int w = n - k - 1;
-                const long long sq = (long long)w * w;
+                const long long sq = (long long)w * (w + 1) / 2;   // the trailing lower triangle
                 for (long long e = tid; e < sq; e += nth) {
-                    const int ii = (int)(e / w), jj = (int)(e % w);
-                    if (jj > ii) continue;
-                    const int i = k + 1 + ii, j = k + 1 + jj;
+                    long long ii, jj;
+                    tri_rc(e, &ii, &jj);
+                    const int i = k + 1 + (int)ii, j = k + 1 + (int)jj;
                     const cx<double> li = colk[i], lj = colk[j];
                     cx<double> gij = G[tri(i, j)];
                     gij.re -= li.re * lj.re + li.im * lj.im;  // l_i conj(l_j)
@@ -398,22 +427,66 @@ static infft_status optimize_impl(infft_plan_s* p, unsigned opts, double* max_re
     int dev = 0, nsm = 0;
     INFFT_CUDA(cudaGetDevice(&dev));
     INFFT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const size_t fixed = (size_t)n_max * (16 * 3 + 8 * g.d + 8);
+    // Two launches.  Columns whose Gram matrix fits in shared memory (with the per-column
+    // arrays) run first, several blocks per SM.  Larger columns (the centre of a linogram
+    // grid holds thousands of members) keep G in global memory; they run largest first on
+    // as many blocks as a share of the free device memory allows.
     const size_t cap = 200 * 1024;
     long long n_smem = 0;
-    while (n_smem < n_max && fixed + (size_t)tri(n_smem + 2, 0) * 16 <= cap) ++n_smem;
-    const size_t smem = fixed + (size_t)tri(n_smem + 1, 0) * 16 + 64;
-    if (fixed + 64 > cap) { set_error("column with %d members exceeds shared memory", n_max); return INFFT_EUNSUPPORTED; }
-    const int blocks = nsm;
-    cx<double>* gscr = nullptr;
-    if (n_smem < n_max) {
-        gscr = (cx<double>*)alloc((size_t)blocks * tri(n_max + 1, 0) * 16);
-        if (!gscr) { set_error("optimize_B: out of device memory (Gram scratch)"); return INFFT_ENOMEM; }
+    while (n_smem < n_max && bopt_fixed_bytes((int)n_smem + 1, g.d) + (size_t)tri(n_smem + 2, 0) * 16 + 64 <= cap)
+        ++n_smem;
+    std::vector<int> small, big;
+    int n_small = 0, n_big = 0;
+    for (long long c = 0; c < ncols; ++c) {
+        const int n = hs[c + 1] - hs[c];
+        if (n <= n_smem) { small.push_back((int)c); n_small = std::max(n_small, n); }
+        else { big.push_back((int)c); n_big = std::max(n_big, n); }
     }
-    INFFT_CUDA(cudaFuncSetAttribute(k_bopt_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_bopt_solve<<<blocks, BOPT_THREADS, smem, st>>>(g, start, members, p->x64, V, rhs2, (int)n_smem, n_max, gscr,
-                                                      (cx<double>*)p->coef64, eps, status);
-    INFFT_LAUNCHED();
+    std::stable_sort(big.begin(), big.end(), [&](int a, int b) { return hs[a + 1] - hs[a] > hs[b + 1] - hs[b]; });
+    int* list = (int*)alloc((small.size() + big.size()) * 4);
+    int* next = (int*)alloc(2 * 4);
+    if (!list || !next) { set_error("optimize_B: out of device memory (column lists)"); return INFFT_ENOMEM; }
+    if (!small.empty())
+        INFFT_CUDA(cudaMemcpyAsync(list, small.data(), small.size() * 4, cudaMemcpyHostToDevice, st));
+    if (!big.empty())
+        INFFT_CUDA(cudaMemcpyAsync(list + small.size(), big.data(), big.size() * 4, cudaMemcpyHostToDevice, st));
+    INFFT_CUDA(cudaMemsetAsync(next, 0, 2 * 4, st));
+    if (!small.empty()) {
+        const size_t smem = bopt_fixed_bytes(std::max(n_small, 1), g.d) + (size_t)tri(n_small + 1, 0) * 16 + 64;
+        int per_sm = 0;
+        INFFT_CUDA(cudaFuncSetAttribute(k_bopt_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        INFFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bopt_solve, BOPT_THREADS, smem));
+        const int blocks = nsm * std::max(1, per_sm);
+        k_bopt_solve<<<blocks, BOPT_THREADS, smem, st>>>(g, start, members, p->x64, V, rhs2, list, (int)small.size(),
+                                                          next, n_small, std::max(n_small, 1), nullptr, 1, nullptr,
+                                                          (cx<double>*)p->coef64, eps, status);
+        INFFT_LAUNCHED();
+    }
+    if (!big.empty()) {
+        const bool fix_smem = bopt_fixed_bytes(n_big, g.d) + 64 <= cap;
+        const size_t per_block = (size_t)tri(n_big + 1, 0) * 16 + (fix_smem ? 0 : bopt_fixed_bytes(n_big, g.d));
+        size_t free_b = 0, total_b = 0;
+        INFFT_CUDA(cudaMemGetInfo(&free_b, &total_b));
+        const long long fit = (long long)((double)free_b * 0.6 / (double)per_block);
+        const int blocks = (int)std::min<long long>(std::min<long long>(nsm, (long long)big.size()), fit);
+        if (blocks < 1) {
+            set_error("optimize_B: a column of %d members needs %zu bytes of Gram scratch, %zu bytes are free",
+                      n_big, per_block, free_b);
+            return INFFT_ENOMEM;
+        }
+        cx<double>* gscr = (cx<double>*)alloc((size_t)blocks * tri(n_big + 1, 0) * 16);
+        unsigned char* gfix = fix_smem ? nullptr : (unsigned char*)alloc((size_t)blocks * bopt_fixed_bytes(n_big, g.d));
+        if (!gscr || (!fix_smem && !gfix)) {
+            set_error("optimize_B: out of device memory (Gram scratch for columns of %d members)", n_big);
+            return INFFT_ENOMEM;
+        }
+        const size_t smem = (fix_smem ? bopt_fixed_bytes(n_big, g.d) : 0) + 16 + 64;
+        INFFT_CUDA(cudaFuncSetAttribute(k_bopt_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_bopt_solve<<<blocks, BOPT_THREADS, smem, st>>>(g, start, members, p->x64, V, rhs2, list + small.size(),
+                                                          (int)big.size(), next + 1, 0, n_big, gscr, fix_smem ? 1 : 0,
+                                                          gfix, (cx<double>*)p->coef64, eps, status);
+        INFFT_LAUNCHED();
+    }
     const int cb = (int)std::min<long long>((nent + 255) / 256, 65535LL * 16);
     if (p->fp64) k_bopt_convert<double><<<cb, 256, 0, st>>>((cx<double>*)p->coef64, nent, (cx<double>*)p->coef);
     else k_bopt_convert<float><<<cb, 256, 0, st>>>((cx<double>*)p->coef64, nent, (cx<float>*)p->coef);

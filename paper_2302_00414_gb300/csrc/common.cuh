@@ -163,6 +163,7 @@ struct Job {
     int nitems, window;        // work items (tile, start, count); window kind
     int mode;                  // INFFT_MODE_*
     int S;                     // B_opt slots per axis (2m+2)
+    int prefetch, fused_fft;   // the plan's tuning of these choices (0 = library default)
     R beta, inv_m;
     const int* perm;           // sorted position -> caller's index
     const uint32_t* cell;      // row-major wrapped base cell of each sorted point
@@ -173,6 +174,7 @@ struct Job {
     const int* tile_items;     // ntile^d + 1 prefix of items per tile
     const R* dinv;             // M entries 1/(Ms w^(k)) (per axis)
     const float* wpoly;        // (WPOLY_DEG + 1) x (2m+1) window polynomial (float32 KB plans) or null
+    const float* wpoly_h;      // host copy of the same table (read by the launchers only) or null
     const cx<R>* tw;           // Ms/2 twiddles exp(-2 pi i k / Ms)
     cx<R>* padded;             // nitems * P^d
     cx<R>* grid;               // Ms^d

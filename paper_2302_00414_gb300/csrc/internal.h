@@ -19,6 +19,7 @@ struct infft_plan_s {
     bool fp64;
     int window;               // infft::WindowKind
     int T, ntile, P, nitems, S;
+    infft_tune_t tune = {0, 0, 0, 0, 0};   // caller's tuning (0 = library default)
     int logMs;
     double beta;
 
@@ -37,6 +38,7 @@ struct infft_plan_s {
     void* tw = nullptr;       // Ms/2 complex
     void* dinv_win = nullptr; // M entries for the B_opt window (may alias dinv)
     float* wpoly = nullptr;   // window polynomial table (float32 Kaiser-Bessel plans)
+    std::vector<float> wpoly_host;   // host copy of that table
 
     // weights (device): caller order float64 master + sorted copy in plan precision
     void* w_master = nullptr; // N complex128, caller order
@@ -91,7 +93,7 @@ infft_status read_back(void* dst, const void* src, size_t bytes, cudaStream_t st
 
 // create a plan (argument checks of infft_plan); pooled plans use pool_alloc on `stream`
 infft_status plan_create(int d, int M, int64_t N, const double* x, double sigma, int m, unsigned flags,
-                         cudaStream_t stream, bool pooled, infft_plan_s** out);
+                         cudaStream_t stream, bool pooled, infft_plan_s** out, const infft_tune_t* tune = nullptr);
 // free a plan's memory without a device-wide synchronisation (pooled plans: in stream order)
 void plan_release(infft_plan_s* p);
 
@@ -156,6 +158,16 @@ template <class R>
 infft_status run_jobs(const std::vector<Job<R>>& jobs, cudaStream_t st, bool forward, cudaEvent_t* ev = nullptr);
 template <class R>
 infft_status run_jobs(const Job<R>* jobs, size_t count, cudaStream_t st, bool forward, cudaEvent_t* ev = nullptr);
+
+// Spreading and halo merge of one job into J.grid (the oversampled grid, Ms^d cells), no FFT.
+template <class R>
+infft_status run_spread_grid(const Job<R>& J, cudaStream_t st);
+
+// One adjoint FFT pass with crop and deconvolution along the middle index of J.grid viewed
+// as an (A, Ms, B) tensor, into J.out as nblk blocks along the middle index, block c holding
+// the (A, M/nblk, B) tensor of the indices c M/nblk .. (c+1) M/nblk - 1.
+template <class R>
+infft_status run_fft_axis(const Job<R>& J, long long A, long long B, int nblk, cudaStream_t st);
 
 // The d FFT passes of one job alone (no spreading, merge or interpolation): forward = true
 // maps J.in (M^d over I_M, times J.dinv per axis) to J.grid (Ms^d) with sign +; forward =

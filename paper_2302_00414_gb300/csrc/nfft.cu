@@ -4,6 +4,7 @@
 // inverse FFT passes (Algorithm 2.1 steps 1-2) and tile-sorted interpolation
 // (Algorithm 2.1 step 3).
 #include <algorithm>
+#include <memory>
 #include <type_traits>
 #include <vector>
 
@@ -123,26 +124,54 @@ __global__ void __launch_bounds__(256) k_merge2d(const __grid_constant__ JobSet<
     const int T = J.T, m = J.m, P = J.P, nt = J.ntile, Ms = J.Ms;
     const int tile = gblk - js.pre_merge[jb];
     const int ty = tile / nt, tx = tile - ty * nt;
+    // work-item ranges of the 3 x 3 tiles around this one, read once per block, so that each
+    // thread's loads of the padded cells do not wait on a load of the item prefix
+    __shared__ int s_i0[9], s_i1[9];
+    if (threadIdx.x < 9) {
+        const int dy = (int)threadIdx.x / 3 - 1, dx = (int)threadIdx.x % 3 - 1;
+        const int tl = mod_pos(ty + dy, nt) * nt + mod_pos(tx + dx, nt);
+        s_i0[threadIdx.x] = J.tile_items[tl];
+        s_i1[threadIdx.x] = J.tile_items[tl + 1];
+    }
+    __syncthreads();
     const int r = threadIdx.x >> 4, c = threadIdx.x & 15;
     if (r >= T || c >= T) return;
-    int yt[2], yo[2], xt[2], xo[2];
+    int yd[2], yo[2], xd[2], xo[2];   // tile offsets (-1, 0, +1) and padded offsets per axis
     int ny = 1, nx = 1;
-    yt[0] = ty; yo[0] = r + m;
-    xt[0] = tx; xo[0] = c + m;
-    if (r + T + m < P) { yt[1] = (ty - 1 + nt) % nt; yo[1] = r + T + m; ny = 2; }
-    else if (r - T + m >= 0) { yt[1] = (ty + 1) % nt; yo[1] = r - T + m; ny = 2; }
-    if (c + T + m < P) { xt[1] = (tx - 1 + nt) % nt; xo[1] = c + T + m; nx = 2; }
-    else if (c - T + m >= 0) { xt[1] = (tx + 1) % nt; xo[1] = c - T + m; nx = 2; }
+    yd[0] = 0; yo[0] = r + m;
+    xd[0] = 0; xo[0] = c + m;
+    if (r + T + m < P) { yd[1] = -1; yo[1] = r + T + m; ny = 2; }
+    else if (r - T + m >= 0) { yd[1] = 1; yo[1] = r - T + m; ny = 2; }
+    if (c + T + m < P) { xd[1] = -1; xo[1] = c + T + m; nx = 2; }
+    else if (c - T + m >= 0) { xd[1] = 1; xo[1] = c - T + m; nx = 2; }
     const size_t cells = (size_t)P * P;
-    cx<R> acc = mk<R>(0, 0);
-    for (int a = 0; a < ny; ++a) {
-        for (int b = 0; b < nx; ++b) {
-            const int tl = yt[a] * nt + xt[b];
-            const int i0 = J.tile_items[tl], i1 = J.tile_items[tl + 1];
-            const size_t off = (size_t)yo[a] * P + xo[b];
-#pragma unroll 4
-            for (int itm = i0; itm < i1; ++itm) acc = add(acc, J.padded[(size_t)itm * cells + off]);
+    // the first item of every source, loaded together; then the sum in source order
+    int i0[4], n[4];
+    size_t off[4];
+    cx<R> v[4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int q = 2 * a + b;
+            n[q] = 0;
+            off[q] = 0;
+            i0[q] = 0;
+            if (a < ny && b < nx) {
+                const int k = (yd[a] + 1) * 3 + xd[b] + 1;
+                i0[q] = s_i0[k];
+                n[q] = s_i1[k] - s_i0[k];
+                off[q] = (size_t)yo[a] * P + xo[b];
+            }
         }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = n[q] > 0 ? J.padded[(size_t)i0[q] * cells + off[q]] : mk<R>(0, 0);
+    cx<R> acc = mk<R>(0, 0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (n[q] <= 0) continue;
+        acc = add(acc, v[q]);
+        for (int k = 1; k < n[q]; ++k) acc = add(acc, J.padded[(size_t)(i0[q] + k) * cells + off[q]]);
     }
     J.grid[(size_t)(ty * T + r) * Ms + tx * T + c] = acc;
 }
@@ -274,8 +303,10 @@ __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> j
     const int lb = gblk - js.pre_fft[pass][jb];
     const int Ms = J.Ms, M = J.M, L = js.L;
     const int t = FWD ? pass : D - 1 - pass;
-    const long long A = ipow(Ms, t);
-    const long long B = ipow(M, D - 1 - t);
+    const bool expl = !FWD && js.axA > 0;   // one explicit pass over an (A, Ms, B) tensor
+    const long long A = expl ? js.axA : ipow(Ms, t);
+    const long long B = expl ? js.axB : ipow(M, D - 1 - t);
+    const int MB = expl ? M / js.axblk : M;   // output block along the middle index
     const int n = Ms;
     const int ns = n + (n >> 4);    // skewed line stride
     const int logn = 31 - __clz(n);
@@ -288,7 +319,10 @@ __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> j
 
     const cx<R>* src;
     cx<R>* dst;
-    if (!FWD) {
+    if (expl) {
+        src = J.grid;
+        dst = J.out;
+    } else if (!FWD) {
         src = (pass == 0) ? J.grid : (pass == 1 ? J.tmp1 : J.tmp2);
         dst = (pass == D - 1) ? J.out : (pass == 0 ? J.tmp1 : J.tmp2);
     } else {
@@ -307,7 +341,7 @@ __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> j
         if (q < nlines) {
             const long long a = q / B, b = q - a * B;
             bi = (a * (FWD ? M : n)) * B + b;
-            bo = (a * (FWD ? n : M)) * B + b;
+            bo = (a * (FWD ? n : MB)) * B + b;
         }
         s_in[tid] = bi;
         s_out[tid] = bo;
@@ -394,7 +428,9 @@ __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> j
             const long long g0 = s_out[l];
             if (g0 >= 0) {
                 const int bin = mod_pos(i - M / 2, Ms);
-                dst[g0 + (long long)i * B] = scale(buf[l * ns + skew(bin)], J.dinv[i]);
+                // block i / MB of the middle index holds the (A, MB, B) tensor of its indices
+                const long long o = (long long)(i / MB) * A * MB * B + (long long)(i % MB) * B;
+                dst[g0 + o] = scale(buf[l * ns + skew(bin)], J.dinv[i]);
             }
         }
     } else {
@@ -545,6 +581,16 @@ static size_t spread_smem_per_warp(const JobSet<R>& js, int D) {
     return mx;
 }
 
+// a JobSet of the listed jobs of js (prefixes not yet filled), on the heap
+template <class R>
+static JobSet<R>* new_subset(const JobSet<R>& js, const std::vector<int>& idx) {
+    JobSet<R>* s = new JobSet<R>();
+    memset(s, 0, sizeof(*s));
+    s->njobs = (int)idx.size();
+    for (int i = 0; i < s->njobs; ++i) s->job[i] = js.job[idx[i]];
+    return s;
+}
+
 // pruned FFT passes with deconvolution, common to every spreading variant
 template <class R, int D>
 static infft_status launch_fft_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* ev) {
@@ -561,20 +607,36 @@ static infft_status launch_fft_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent
 }
 
 template <class R, int D>
-static infft_status launch_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* ev) {
+static infft_status launch_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* ev, bool grid_only = false) {
     fill_prefixes(js, D, false);
     if (ev) INFFT_CUDA(cudaEventRecord(ev[0], st));
     bool used = false;
     if (D == 2) INFFT_TRY(spread2d_try<R>(js, st, &used));
     if (used) {
         if (ev) INFFT_CUDA(cudaEventRecord(ev[1], st));
-        // merge: one block per tile
-        js.pre_merge[0] = 0;
-        for (int j = 0; j < js.njobs; ++j) js.pre_merge[j + 1] = js.pre_merge[j] + js.job[j].ntile * js.job[j].ntile;
-        k_merge2d<R><<<js.pre_merge[js.njobs], 256, 0, st>>>(js);
+        // merge and FFT passes fused in one cluster kernel per grid size where it applies
+        std::vector<int> rest;
+        if (grid_only) {
+            for (int j = 0; j < js.njobs; ++j) rest.push_back(j);
+        } else {
+            INFFT_TRY(mergefft2d_try<R>(js, st, rest));
+        }
+        if (rest.empty()) {
+            if (ev)
+                for (int k = 2; k < 3 + D; ++k) INFFT_CUDA(cudaEventRecord(ev[k], st));
+            return INFFT_OK;
+        }
+        // the other jobs: merge (one block per tile), then the FFT passes
+        JobSet<R>& jr = (int)rest.size() == js.njobs ? js : *new_subset(js, rest);
+        std::unique_ptr<JobSet<R>> own(&jr == &js ? nullptr : &jr);
+        if (own) fill_prefixes(jr, D, false);
+        jr.pre_merge[0] = 0;
+        for (int j = 0; j < jr.njobs; ++j) jr.pre_merge[j + 1] = jr.pre_merge[j] + jr.job[j].ntile * jr.job[j].ntile;
+        k_merge2d<R><<<jr.pre_merge[jr.njobs], 256, 0, st>>>(jr);
         INFFT_LAUNCHED();
         if (ev) INFFT_CUDA(cudaEventRecord(ev[2], st));
-        return launch_fft_adjoint<R, D>(js, st, ev);
+        if (grid_only) return INFFT_OK;
+        return launch_fft_adjoint<R, D>(jr, st, ev);
     }
     if (D == 3) INFFT_TRY(spread3d_try<R>(js, st, &used));
     if (used) {
@@ -587,6 +649,7 @@ static infft_status launch_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* 
         k_merge3d<R><<<js.pre_merge[js.njobs], 256, 0, st>>>(js);
         INFFT_LAUNCHED();
         if (ev) INFFT_CUDA(cudaEventRecord(ev[2], st));
+        if (grid_only) return INFFT_OK;
         return launch_fft_adjoint<R, D>(js, st, ev);
     }
     const size_t spw = spread_smem_per_warp(js, D);
@@ -608,6 +671,7 @@ static infft_status launch_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* 
     k_merge<R, D><<<js.pre_merge[js.njobs], 256, 0, st>>>(js);
     INFFT_LAUNCHED();
     if (ev) INFFT_CUDA(cudaEventRecord(ev[2], st));
+    if (grid_only) return INFFT_OK;
     return launch_fft_adjoint<R, D>(js, st, ev);
 }
 
@@ -697,6 +761,47 @@ static infft_status fft_passes_d(JobSet<R>& js, cudaStream_t st, bool forward) {
     }
     return INFFT_OK;
 }
+
+template <class R>
+infft_status run_spread_grid(const Job<R>& J, cudaStream_t st) {
+    JobSet<R> js;
+    memset(&js, 0, sizeof(js));
+    js.njobs = 1;
+    js.job[0] = J;
+    switch (J.d) {
+        case 1: return launch_adjoint<R, 1>(js, st, nullptr, true);
+        case 2: return launch_adjoint<R, 2>(js, st, nullptr, true);
+        default: return launch_adjoint<R, 3>(js, st, nullptr, true);
+    }
+}
+
+template <class R>
+infft_status run_fft_axis(const Job<R>& J, long long A, long long B, int nblk, cudaStream_t st) {
+    JobSet<R> js;
+    memset(&js, 0, sizeof(js));
+    js.njobs = 1;
+    js.job[0] = J;
+    js.axA = A;
+    js.axB = B;
+    js.axblk = nblk;
+    const int n = J.Ms;
+    js.L = pick_lines(n, sizeof(cx<R>));
+    const long long lines = A * B;
+    if ((lines + js.L - 1) / js.L >= (1ll << 31)) {
+        set_error("too many FFT lines");
+        return INFFT_EUNSUPPORTED;
+    }
+    js.pre_fft[0][1] = (int)((lines + js.L - 1) / js.L);
+    const size_t fsmem = ((size_t)js.L * (n + n / 16) + n / 2) * sizeof(cx<R>);
+    INFFT_CUDA(cudaFuncSetAttribute(k_fft<R, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
+    k_fft<R, 2, false><<<js.pre_fft[0][1], 256, fsmem, st>>>(js, 0);
+    INFFT_LAUNCHED();
+    return INFFT_OK;
+}
+template infft_status run_spread_grid<float>(const Job<float>&, cudaStream_t);
+template infft_status run_spread_grid<double>(const Job<double>&, cudaStream_t);
+template infft_status run_fft_axis<float>(const Job<float>&, long long, long long, int, cudaStream_t);
+template infft_status run_fft_axis<double>(const Job<double>&, long long, long long, int, cudaStream_t);
 
 template <class R>
 infft_status run_fft_passes(const Job<R>& J, cudaStream_t st, bool forward) {

@@ -120,6 +120,17 @@ infft_status dev_alloc(infft_plan_s* p, void** ptr, size_t bytes) {
     return INFFT_OK;
 }
 
+// page-locked host memory (cudaHostAlloc / cudaHostRegister): copies from and to it can be
+// captured into a CUDA graph
+static bool is_pinned_host_pointer(const void* ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 bool is_device_pointer(const void* ptr) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
@@ -334,6 +345,7 @@ Job<R> make_job(const infft_plan_s* p, int mode, const void* in, void* out, int 
     // (the plan's P, which sizes the scratch)
     J.P = (mode == INFFT_MODE_BOPT) ? p->P : p->T + 2 * p->m;
     J.nitems = p->nitems; J.window = p->window; J.mode = mode; J.S = p->S;
+    J.prefetch = p->tune.prefetch; J.fused_fft = p->tune.fused_fft;
     J.beta = (R)p->beta; J.inv_m = (R)(1.0 / p->m);
     J.perm = p->perm; J.cell = p->cell; J.u = (const R*)p->u;
     J.w = (const cx<R>*)p->w_sorted; J.coef = (const cx<R>*)p->coef;
@@ -341,6 +353,7 @@ Job<R> make_job(const infft_plan_s* p, int mode, const void* in, void* out, int 
     J.dinv = (mode == INFFT_MODE_BOPT && p->dinv_win) ? (const R*)p->dinv_win : (const R*)p->dinv;
     J.tw = (const cx<R>*)p->tw;
     J.wpoly = p->wpoly;
+    J.wpoly_h = p->wpoly_host.empty() ? nullptr : p->wpoly_host.data();
     if (slot == 0) {
         J.padded = (cx<R>*)p->padded; J.grid = (cx<R>*)p->grid;
         J.tmp1 = (cx<R>*)p->tmp1; J.tmp2 = (cx<R>*)p->tmp2;
@@ -380,7 +393,11 @@ static infft_status build_plan(infft_plan_s* p, const double* x_in, cudaStream_t
 
     // tiles: T^d cells, T > m
     const int Tdef = d == 1 ? 256 : (d == 2 ? 16 : 8);
-    p->T = std::min(Tdef, Ms);
+    p->T = p->tune.tile > 0 ? p->tune.tile : std::min(Tdef, Ms);
+    if (p->T > Ms || (p->T & (p->T - 1))) {
+        set_error("tile edge %d must be a power of two <= M_sigma = %d", p->T, Ms);
+        return INFFT_EINVAL;
+    }
     if (p->T <= m) {
         set_error("tile edge %d must exceed m = %d", p->T, m);
         return INFFT_EUNSUPPORTED;
@@ -462,7 +479,7 @@ static infft_status build_plan(infft_plan_s* p, const double* x_in, cudaStream_t
     INFFT_TRY(read_back(cs.data(), count, (size_t)(nkeys + 1) * 4, st));
     INFFT_CUDA(cudaStreamSynchronize(st));
     // d = 1: short items so that a few hundred points still spread on several warps
-    const int cap = d == 1 ? 32 : 512;
+    const int cap = p->tune.item_cap > 0 ? p->tune.item_cap : (d == 1 ? 32 : 512);
     std::vector<int4> items;
     std::vector<int> tile_items(ntiles + 1, 0);
     for (int tl = 0; tl < ntiles; ++tl) {
@@ -498,6 +515,9 @@ static infft_status build_plan(infft_plan_s* p, const double* x_in, cudaStream_t
         INFFT_TRY(dev_alloc(p, (void**)&p->wpoly, (size_t)(WPOLY_DEG + 1) * wpoly_stride(2 * m + 1) * sizeof(float)));
         k_wpoly<<<1, 32, 0, st>>>(m, p->beta, p->wpoly);
         INFFT_LAUNCHED();
+        p->wpoly_host.resize((size_t)(WPOLY_DEG + 1) * wpoly_stride(2 * m + 1));
+        INFFT_CUDA(cudaMemcpyAsync(p->wpoly_host.data(), p->wpoly, p->wpoly_host.size() * sizeof(float),
+                                   cudaMemcpyDeviceToHost, st));
     }
 
     // scratch
@@ -522,9 +542,15 @@ static infft_status build_plan(infft_plan_s* p, const double* x_in, cudaStream_t
 }
 
 infft_status plan_create(int d, int M, int64_t N, const double* x, double sigma, int m, unsigned flags,
-                         cudaStream_t stream, bool pooled, infft_plan_s** out) {
+                         cudaStream_t stream, bool pooled, infft_plan_s** out, const infft_tune_t* tune) {
     if (!out) { set_error("out is NULL"); return INFFT_EINVAL; }
     *out = nullptr;
+    if (tune && (tune->tile < 0 || tune->item_cap < 0 || tune->branches < 0 || tune->branches > 8 ||
+                 tune->prefetch < 0 || tune->prefetch > 2 || tune->fused_fft < 0 || tune->fused_fft > 2)) {
+        set_error("invalid tuning (tile %d, item_cap %d, branches %d, prefetch %d, fused_fft %d)", tune->tile,
+                  tune->item_cap, tune->branches, tune->prefetch, tune->fused_fft);
+        return INFFT_EINVAL;
+    }
     if (d < 1 || d > 3 || M < 2 || (M & 1) || N < 1 || N >= (1ll << 31) || !x || !(sigma >= 1.0) || m < 1) {
         set_error("invalid plan arguments (d=%d M=%d N=%lld sigma=%g m=%d)", d, M, (long long)N, sigma, m);
         return INFFT_EINVAL;
@@ -543,6 +569,12 @@ infft_status plan_create(int d, int M, int64_t N, const double* x, double sigma,
     while ((1 << l) < Ms) ++l;
     p->logMs = l;
     p->pooled = pooled || (flags & INFFT_POOLED) != 0;
+    if (tune) p->tune = *tune;
+    if (p->tune.tile > 0 && p->tune.tile <= m) {
+        set_error("tile edge %d must exceed m = %d", p->tune.tile, m);
+        delete p;
+        return INFFT_EINVAL;
+    }
     p->pool_stream = stream;
     infft_status s = build_plan(p, x, stream);
     if (s != INFFT_OK) { free_plan(p); return s; }
@@ -563,6 +595,11 @@ void infft_launch_count_reset(void) { g_launches = 0; }
 infft_status infft_plan(int d, int M, int64_t N, const double* x, double sigma, int m, unsigned flags, void* stream,
                         infft_plan_t* out) {
     return plan_create(d, M, N, x, sigma, m, flags, (cudaStream_t)stream, false, out);
+}
+
+infft_status infft_plan_tuned(int d, int M, int64_t N, const double* x, double sigma, int m, unsigned flags,
+                              const infft_tune_t* tune, void* stream, infft_plan_t* out) {
+    return plan_create(d, M, N, x, sigma, m, flags, (cudaStream_t)stream, false, out, tune);
 }
 
 void infft_inject_faults(unsigned mask) { g_fault_mask.store((int)(mask & 7u), std::memory_order_relaxed); }
@@ -659,6 +696,48 @@ static infft_status transform(infft_plan_t p, int mode, const void* in, void* ou
         INFFT_CUDA(cudaStreamSynchronize(st));
     }
     return INFFT_OK;
+}
+
+infft_status infft_spread_grid(infft_plan_t p, int mode, const void* f, void* grid, void* stream) {
+    if (!p || !f || !grid) { set_error("null argument"); return INFFT_EINVAL; }
+    INFFT_TRY(check_mode(p, mode));
+    if (!is_device_pointer(f) || !is_device_pointer(grid)) {
+        set_error("infft_spread_grid: f and grid must be device pointers");
+        return INFFT_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    p->pool_stream = st;
+    if (p->fp64) {
+        Job<double> J = make_job<double>(p, mode, f, nullptr);
+        J.grid = (cx<double>*)grid;
+        return run_spread_grid<double>(J, st);
+    }
+    Job<float> J = make_job<float>(p, mode, f, nullptr);
+    J.grid = (cx<float>*)grid;
+    return run_spread_grid<float>(J, st);
+}
+
+infft_status infft_fft_axis(infft_plan_t p, int mode, int64_t A, int64_t B, int nblk, const void* in, void* out,
+                            void* stream) {
+    if (!p || !in || !out) { set_error("null argument"); return INFFT_EINVAL; }
+    if (A < 1 || B < 1 || nblk < 1 || p->M % nblk) {
+        set_error("infft_fft_axis: A = %lld, B = %lld, nblk = %d (M = %d)", (long long)A, (long long)B, nblk, p->M);
+        return INFFT_EINVAL;
+    }
+    INFFT_TRY(check_mode(p, mode));
+    if (!is_device_pointer(in) || !is_device_pointer(out)) {
+        set_error("infft_fft_axis: in and out must be device pointers");
+        return INFFT_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p->fp64) {
+        Job<double> J = make_job<double>(p, mode, nullptr, out);
+        J.grid = (cx<double>*)in;
+        return run_fft_axis<double>(J, A, B, nblk, st);
+    }
+    Job<float> J = make_job<float>(p, mode, nullptr, out);
+    J.grid = (cx<float>*)in;
+    return run_fft_axis<float>(J, A, B, nblk, st);
 }
 
 infft_status infft_adjoint(infft_plan_t p, int mode, const void* f, void* fhat, void* stream) {
@@ -784,9 +863,10 @@ static infft_status run_batched(const infft_plan_t* plans, int count, int mode, 
 // buffers the copies gain from more branches (end to end 1 / 3 / 6 / 8 branches: 39.8k /
 // 53.8k / 57.4k / 63.4k reconstructions/s before later kernel changes), so those calls take 8.
 // The environment variable INFFT_BATCH_BRANCHES (1..8) overrides both.
-static int branch_count(int count, bool host_buffers = false) {
+static int branch_count(const infft_plan_t* plans, int count, bool host_buffers = false) {
     int G = host_buffers ? 8 : 3;
-    if (const char* env = getenv("INFFT_BATCH_BRANCHES")) G = std::max(1, std::min(8, atoi(env)));
+    if (plans[0]->tune.branches > 0) G = plans[0]->tune.branches;
+    else if (const char* env = getenv("INFFT_BATCH_BRANCHES")) G = std::max(1, std::min(8, atoi(env)));
     return std::max(1, std::min(G, count));
 }
 
@@ -843,7 +923,7 @@ static infft_status run_branched(const infft_plan_t* plans, int count, int mode,
         host_out = host_out || !is_device_pointer(fhat[i]);
         host_in = host_in || !is_device_pointer(f[i]);
     }
-    const int G = branch_count(count, host_in || host_out);
+    const int G = branch_count(plans, count, host_in || host_out);
     if (G == 1) return run_batched(plans, count, mode, f, fhat, st, nullptr, slot.data());
     BranchSet* b = nullptr;
     INFFT_TRY(branch_set(st, &b));
@@ -912,13 +992,18 @@ infft_status infft_batch_create(const infft_plan_t* plans, int count, int mode, 
     // scratch sets over the whole batch, allocated outside the capture
     std::vector<int> slot;
     INFFT_TRY(prepare_batched(plans, count, f, fhat, nullptr, slot, (cudaStream_t)stream));
-    for (int i = 0; i < count; ++i)
-        if (!is_device_pointer(f[i]) || !is_device_pointer(fhat[i])) {
-            set_error("graph batches need device buffers");
+    // device buffers, or page-locked host buffers whose copies the graph then holds
+    bool host = false;
+    for (int i = 0; i < count; ++i) {
+        const bool hi = !is_device_pointer(f[i]), ho = !is_device_pointer(fhat[i]);
+        if ((hi && !is_pinned_host_pointer(f[i])) || (ho && !is_pinned_host_pointer(fhat[i]))) {
+            set_error("graph batches need device or page-locked host buffers (job %d)", i);
             return INFFT_EINVAL;
         }
+        host = host || hi || ho;
+    }
     // the jobs in concurrent branches of unequal work, as in run_branched
-    const int G = branch_count(count);
+    const int G = branch_count(plans, count, host);
     const std::vector<std::vector<int>> grp = split_groups(plans, count, G);
     cudaStream_t cap;
     INFFT_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
@@ -941,7 +1026,8 @@ infft_status infft_batch_create(const infft_plan_t* plans, int count, int mode, 
             std::vector<void*> H;
             std::vector<int> S;
             for (int i : grp[g]) { P.push_back(plans[i]); F.push_back(f[i]); H.push_back(fhat[i]); S.push_back(slot[i]); }
-            if (!P.empty()) s = run_batched(P.data(), (int)P.size(), mode, F.data(), H.data(), br[g], nullptr, S.data());
+            if (!P.empty())
+                s = run_batched(P.data(), (int)P.size(), mode, F.data(), H.data(), br[g], nullptr, S.data(), false);
             cudaEventRecord(ev[g], br[g]);
             cudaStreamWaitEvent(cap, ev[g], 0);
         }

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cstdlib>
+#include <vector>
 
 #include "internal.h"
 #include "jobset.cuh"
@@ -35,6 +36,12 @@ infft_status spread2d_try(JobSet<R>& js, cudaStream_t st, bool* used);
 // *used tells whether it did.
 template <class R>
 infft_status spread3d_try(JobSet<R>& js, cudaStream_t st, bool* used);
+
+// Halo merge and both pruned FFT passes (with deconvolution) of d = 2 adjoint jobs as one
+// thread-block-cluster kernel per grid size, for the jobs whose grid it takes; `rest`
+// receives the indices of the jobs left to the two-kernel form.
+template <class R>
+infft_status mergefft2d_try(const JobSet<R>& js, cudaStream_t st, std::vector<int>& rest);
 
 // Launch the fixed-m interpolation for d = 2 (m <= 8) or d = 3 (m <= 6) when every job has
 // the same m and power-of-two tiles and grids; *used tells whether it did.  The FFT passes

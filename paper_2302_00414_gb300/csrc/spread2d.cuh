@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
 #include <type_traits>
 
 #include "spread.cuh"
@@ -23,6 +24,12 @@ constexpr bool spread2d_pair_m(int m) { return sizeof(R) == 4 && m <= 4; }   // 
 // the 8-byte column pairs of the paired form
 template <class R, int MM, bool BOPT>
 __host__ __device__ constexpr int spread2d_pitch() { return spread2d_pair<R, MM, BOPT>() ? 34 : 33; }
+
+// row stride (complex elements) of the staged c_j psi_y: W in the paired form, whose rows are
+// read with 8-byte broadcasts (an odd stride of 8-byte words: the staging stores of 32 lanes
+// hit distinct banks), W + 1 elsewhere, whose rows are read with 16-byte broadcasts
+template <class R, int MM, bool BOPT>
+__host__ __device__ constexpr int spread2d_we() { return spread2d_pair<R, MM, BOPT>() ? 2 * MM + 1 : 2 * MM + 2; }
 
 // bytes of the per-warp prefetch slots (w, u pairs, perm, cell of 32 points); a multiple of 16
 template <class R, bool PF>
@@ -51,7 +58,7 @@ template <class R, int MM, bool BOPT, bool PF>
 __global__ void __launch_bounds__(128, spread2d_pair<R, MM, BOPT>() ? 5 : 1)
     k_spread2d(const __grid_constant__ JobSet<R> js) {
     constexpr int W = 2 * MM + 1;              // window taps per axis
-    constexpr int WE = W + 1;                  // even stride of the staged rows (16-byte loads)
+    constexpr int WE = spread2d_we<R, MM, BOPT>();   // stride of the staged rows
     constexpr int WR = BOPT ? W + 1 : W;       // rows held in registers
     constexpr bool F32 = sizeof(R) == 4;
     constexpr bool PAIR = spread2d_pair<R, MM, BOPT>();
@@ -80,8 +87,11 @@ __global__ void __launch_bounds__(128, spread2d_pair<R, MM, BOPT>() ? 5 : 1)
     int* meta = reinterpret_cast<int*>(psx + 32 * PX);      // [32][3]  oy, ox, sorted index
     cx<R>* cst = reinterpret_cast<cx<R>*>(meta + 96);       // [32]     c_j (B_opt mode)
     float* poly = reinterpret_cast<float*>(cst + 32);       // [(WPOLY_DEG+1) * WP] window polynomial (16-byte rows)
+    // the paired form evaluates the taps from the parameter block when every job shares one
+    // window polynomial (js.wtab_ok), else from a copy in shared memory
+    const bool tab_param = PAIR && js.wtab_ok;
     const bool use_poly = F32 && !BOPT && J.wpoly != nullptr;
-    if (use_poly) {
+    if (use_poly && !tab_param) {
         for (int e = lane; e < (WPOLY_DEG + 1) * wpoly_stride(W); e += 32) poly[e] = J.wpoly[e];
     }
 
@@ -153,7 +163,10 @@ __global__ void __launch_bounds__(128, spread2d_pair<R, MM, BOPT>() ? 5 : 1)
                 R wy[W], wx[W];
                 bool done = false;
                 if constexpr (F32) {
-                    if (use_poly) {
+                    if (tab_param) {
+                        poly_taps2<W>(js.wtab, uy, ux, wy, wx);
+                        done = true;
+                    } else if (use_poly) {
                         poly_taps2<W>(poly, uy, ux, wy, wx);
                         done = true;
                     }
@@ -181,7 +194,7 @@ __global__ void __launch_bounds__(128, spread2d_pair<R, MM, BOPT>() ? 5 : 1)
                     cy[lane * WE + s] = scale(fv, wy[s]);
                     row[oxl + s] = wx[s];
                 }
-                cy[lane * WE + W] = mk<R>(0, 0);
+                if (WE > W) cy[lane * WE + W] = mk<R>(0, 0);   // the pad the 16-byte row loads read
             }
         }
         __syncwarp();   // orders every read of the prefetch slots before their refill
@@ -210,17 +223,14 @@ __global__ void __launch_bounds__(128, spread2d_pair<R, MM, BOPT>() ? 5 : 1)
                     float2 wv = *reinterpret_cast<const float2*>(psx + pr * PX + 2 * hl);
                     if (!act) wv = make_float2(0.f, 0.f);
                     const float2 wa = make_float2(wv.x, wv.x), wb = make_float2(wv.y, wv.y);
-                    const float4* cp4 = reinterpret_cast<const float4*>(cy + pr * WE);
+                    // one 8-byte broadcast per row: the two halves read two points' rows in
+                    // one wavefront
+                    const float2* cp2 = reinterpret_cast<const float2*>(cy + pr * WE);
 #pragma unroll
-                    for (int k2 = 0; k2 < WE / 2; ++k2) {
-                        const float4 c = cp4[k2];
-                        const float2 c0 = make_float2(c.x, c.y), c1 = make_float2(c.z, c.w);
-                        acc[4 * k2] = __ffma2_rn(c0, wa, acc[4 * k2]);
-                        acc[4 * k2 + 1] = __ffma2_rn(c0, wb, acc[4 * k2 + 1]);
-                        if (2 * k2 + 1 < W) {
-                            acc[4 * k2 + 2] = __ffma2_rn(c1, wa, acc[4 * k2 + 2]);
-                            acc[4 * k2 + 3] = __ffma2_rn(c1, wb, acc[4 * k2 + 3]);
-                        }
+                    for (int k = 0; k < W; ++k) {
+                        const float2 c = cp2[k];
+                        acc[2 * k] = __ffma2_rn(c, wa, acc[2 * k]);
+                        acc[2 * k + 1] = __ffma2_rn(c, wb, acc[2 * k + 1]);
                     }
                 }
                 p = q;
@@ -281,9 +291,21 @@ __global__ void __launch_bounds__(128, spread2d_pair<R, MM, BOPT>() ? 5 : 1)
 template <class R, int MM, bool BOPT, bool PF>
 static infft_status launch_spread2d_m(JobSet<R>& js, cudaStream_t st) {
     constexpr int W = 2 * MM + 1;
-    constexpr int WE = W + 1;
+    constexpr int WE = spread2d_we<R, MM, BOPT>();
     size_t spw = spread2d_slot_bytes<R, PF>() + 32 * WE * sizeof(cx<R>) + 32 * spread2d_pitch<R, MM, BOPT>() * sizeof(R) + 96 * sizeof(int) + 32 * sizeof(cx<R>) +
                  (WPOLY_DEG + 1) * wpoly_stride(W) * sizeof(float);
+    // one window polynomial for every job: into the parameter block
+    js.wtab_ok = 0;
+    if (spread2d_pair<R, MM, BOPT>() && wpoly_stride(W) <= 12) {
+        const size_t n = (size_t)(WPOLY_DEG + 1) * wpoly_stride(W);
+        bool same = js.job[0].wpoly_h != nullptr;
+        for (int j = 1; j < js.njobs && same; ++j)
+            same = js.job[j].wpoly_h && memcmp(js.job[j].wpoly_h, js.job[0].wpoly_h, n * sizeof(float)) == 0;
+        if (same) {
+            memcpy(js.wtab, js.job[0].wpoly_h, n * sizeof(float));
+            js.wtab_ok = 1;
+        }
+    }
     spw = (spw + 15) & ~(size_t)15;
     js.smem_per_warp = (int)spw;
     js.wpb = 4;
@@ -319,7 +341,8 @@ static bool aligned(const void* p, size_t a) { return ((uintptr_t)p & (a - 1)) =
 // form regardless (both give the same sums in the same order).
 template <class R>
 static bool spread2d_prefetch(const JobSet<R>& js, int m) {
-    const int env = env_form("INFFT_SPREAD2D_PREFETCH");
+    // the first job's plan tuning (1 on, 2 off) comes first, then the environment
+    const int env = js.job[0].prefetch == 1 ? 1 : js.job[0].prefetch == 2 ? 0 : env_form("INFFT_SPREAD2D_PREFETCH");
     if (env == 0) return false;
     if (env != 1 && !spread2d_pair_m<R>(m)) {
         int dev = 0, nsm = 0;

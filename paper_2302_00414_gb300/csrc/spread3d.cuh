@@ -259,7 +259,8 @@ static bool aligned3(const void* p, size_t a) { return ((uintptr_t)p & (a - 1)) 
 // in the same order) or a copy it would make is misaligned.
 template <class R>
 static bool spread3d_prefetch(const JobSet<R>& js) {
-    if (env_form("INFFT_SPREAD3D_PREFETCH") == 0) return false;
+    // the first job's plan tuning (1 on, 2 off) comes first, then the environment
+    if (js.job[0].prefetch == 2 || (js.job[0].prefetch == 0 && env_form("INFFT_SPREAD3D_PREFETCH") == 0)) return false;
     for (int j = 0; j < js.njobs; ++j) {
         const Job<R>& J = js.job[j];
         if (!aligned3(J.perm, 4) || !aligned3(J.cell, 4) || !aligned3(J.u, sizeof(R)) ||

@@ -68,15 +68,33 @@ __global__ void k_dot_final(const double* __restrict__ part, double* __restrict_
     if (threadIdx.x == 0) { out[0] = sre[0]; out[1] = sim[0]; }
 }
 
-// CG scalars: s[0] = rr, s[2] = <p, q>, s[4] = rr_new, s[6] = alpha, s[7] = beta
-__global__ void k_cg_alpha(double* s) { s[6] = (s[2] != 0.0) ? s[0] / s[2] : 0.0; }
-__global__ void k_cg_beta(double* s) {
-    s[7] = (s[0] != 0.0) ? s[4] / s[0] : 0.0;
-    s[0] = s[4];
+// CG scalars, all on the device: s[0] = rr, s[2] = <p, q>, s[4] = rr_new, s[6] = alpha,
+// s[7] = beta, s[10] = smallest rr so far, s[11] = state (0 running, 1 converged, 2 NaN,
+// 3 max_iter reached), s[12] = iterations taken, s[13] = (rel_tol ||b||)^2, s[14] = max_iter,
+// s[15] = this iteration improved on s[10], s[16] = this iteration runs.  Every kernel of an
+// iteration is a no-op once the state is no longer 0, so the host may queue several
+// iterations between looks at the state.
+__global__ void k_cg_begin(double* s) { s[16] = (s[11] == 0.0) ? 1.0 : 0.0; }
+__global__ void k_cg_alpha(double* s) {
+    if (s[16] == 0.0) return;
+    s[6] = (s[2] != 0.0) ? s[0] / s[2] : 0.0;
+}
+__global__ void k_cg_end(double* s) {
+    if (s[16] == 0.0) return;
+    const double rn = s[4];
+    s[12] += 1.0;
+    if (!(rn == rn)) { s[11] = 2.0; s[15] = 0.0; return; }
+    s[15] = (rn < s[10]) ? 1.0 : 0.0;
+    if (rn < s[10]) s[10] = rn;
+    s[7] = (s[0] != 0.0) ? rn / s[0] : 0.0;
+    s[0] = rn;
+    if (rn <= s[13]) s[11] = 1.0;
+    else if (s[12] >= s[14]) s[11] = 3.0;
 }
 
 __global__ void k_cg_update_xr(cx<double>* __restrict__ x, cx<double>* __restrict__ r, const cx<double>* __restrict__ p,
                                const cx<double>* __restrict__ q, long long n, const double* __restrict__ s) {
+    if (s[16] == 0.0) return;
     const double al = s[6];
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         x[i] = add(x[i], scale(p[i], al));
@@ -84,11 +102,34 @@ __global__ void k_cg_update_xr(cx<double>* __restrict__ x, cx<double>* __restric
     }
 }
 
+// x_best = x when this iteration's residual is the smallest so far (the weights come from
+// the best iterate, so that a capped CG never returns worse weights than an earlier step of
+// the same run)
+__global__ void k_cg_keep_best(const cx<double>* __restrict__ x, cx<double>* __restrict__ xb, long long n,
+                               const double* __restrict__ s) {
+    if (s[16] == 0.0 || s[15] == 0.0) return;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        xb[i] = x[i];
+}
+
 __global__ void k_cg_update_p(cx<double>* __restrict__ p, const cx<double>* __restrict__ r, long long n,
                               const double* __restrict__ s) {
+    if (s[16] == 0.0 || s[11] != 0.0) return;
     const double be = s[7];
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         p[i] = add(r[i], scale(p[i], be));
+}
+
+// the CG's starting scalars: rr = ||b||^2, no best iterate yet (the first iteration always
+// becomes the best: x0 = 0 itself is never returned), tolerance and iteration cap
+__global__ void k_cg_init(double* s, double rel_tol, int max_iter) {
+    s[10] = HUGE_VAL;
+    s[11] = 0.0;
+    s[12] = 0.0;
+    s[13] = rel_tol * rel_tol * s[0];
+    s[14] = (double)max_iter;
+    s[15] = 0.0;
+    s[16] = 1.0;
 }
 
 __global__ void k_conj(const cx<double>* __restrict__ a, cx<double>* __restrict__ b, long long n) {
@@ -335,6 +376,7 @@ static infft_status weights_impl(infft_plan_s* p, int max_iter, double rel_tol, 
         return q;
     };
     cx<double>* x = (cx<double>*)alloc(n * 16);
+    cx<double>* xb = (cx<double>*)alloc(n * 16);
     cx<double>* r = (cx<double>*)alloc(n * 16);
     cx<double>* pv = (cx<double>*)alloc(n * 16);
     cx<double>* qv = (cx<double>*)alloc(n * 16);
@@ -342,17 +384,17 @@ static infft_status weights_impl(infft_plan_s* p, int max_iter, double rel_tol, 
     cx<double>* ws = (cx<double>*)alloc((size_t)N * 16);
     cx<double>* kv = (cx<double>*)alloc(K * 16);
     double* part = (double*)alloc(2 * RED_BLOCKS * 8);
-    double* sc = (double*)alloc(16 * 8);
-    double* bn = (double*)alloc(16);
-    if (!x || !r || !pv || !qv || !aux || !ws || !kv || !part || !sc || !bn) {
+    double* sc = (double*)alloc(32 * 8);
+    if (!x || !xb || !r || !pv || !qv || !aux || !ws || !kv || !part || !sc) {
         set_error("CG buffers: out of device memory");
         return INFFT_ENOMEM;
     }
     const int eb = 1024, et = 256;
     ToeplitzOp top;
     if (toeplitz) INFFT_TRY(toeplitz_setup(p, sub, M2, st, [&](size_t b) { return alloc(b); }, top));
-    // x = 0; r = b; p = b
+    // x = x_best = 0; r = b; p = b
     INFFT_CUDA(cudaMemsetAsync(x, 0, n * 16, st));
+    INFFT_CUDA(cudaMemsetAsync(xb, 0, n * 16, st));
     if (second_kind) {
         INFFT_CUDA(cudaMemsetAsync(r, 0, n * 16, st));
         long long k0 = 0;
@@ -364,42 +406,51 @@ static infft_status weights_impl(infft_plan_s* p, int max_iter, double rel_tol, 
         INFFT_LAUNCHED();
     }
     INFFT_CUDA(cudaMemcpyAsync(pv, r, n * 16, cudaMemcpyDeviceToDevice, st));
-    INFFT_TRY(dot(r, r, n, part, sc + 0, st));  // rr
-    INFFT_CUDA(cudaMemcpyAsync(bn, sc + 0, 8, cudaMemcpyDeviceToDevice, st));
-    double b2 = 0;
-    INFFT_TRY(read_back(&b2, bn, 8, st));
-    INFFT_CUDA(cudaStreamSynchronize(st));
-    const double bnorm = std::sqrt(b2);
+    INFFT_TRY(dot(r, r, n, part, sc + 0, st));  // rr = ||b||^2
+    k_cg_init<<<1, 1, 0, st>>>(sc, rel_tol, max_iter);
+    INFFT_LAUNCHED();
 
-    int it = 0;
-    bool conv = false;
-    for (it = 0; it < max_iter; ++it) {
-        // q = op(p)
-        if (toeplitz) {
-            INFFT_TRY(toeplitz_apply(top, pv, qv, st));   // A^* A p as a convolution
-        } else if (second_kind) {
-            INFFT_TRY(nfft64(sub, true, pv, aux, st));    // A p   (K -> N)
-            INFFT_TRY(nfft64(sub, false, aux, qv, st));   // A^* (A p)
-        } else {
-            INFFT_TRY(nfft64(sub, false, pv, aux, st));   // A^* p (N -> K)
-            INFFT_TRY(nfft64(sub, true, aux, qv, st));    // A (A^* p)
+    // Iterations are queued in chunks of up to eight; the device's state flag makes the
+    // queued iterations after convergence no-ops, and the host reads the state once per chunk
+    // (no synchronisation inside a chunk).
+    int queued = 0;
+    double state[3] = {0, 0, 0};   // state, iterations, best rr
+    while (queued < max_iter) {
+        const int chunk = std::min(8, max_iter - queued);
+        for (int c = 0; c < chunk; ++c) {
+            k_cg_begin<<<1, 1, 0, st>>>(sc);
+            INFFT_LAUNCHED();
+            // q = op(p)
+            if (toeplitz) {
+                INFFT_TRY(toeplitz_apply(top, pv, qv, st));   // A^* A p as a convolution
+            } else if (second_kind) {
+                INFFT_TRY(nfft64(sub, true, pv, aux, st));    // A p   (K -> N)
+                INFFT_TRY(nfft64(sub, false, aux, qv, st));   // A^* (A p)
+            } else {
+                INFFT_TRY(nfft64(sub, false, pv, aux, st));   // A^* p (N -> K)
+                INFFT_TRY(nfft64(sub, true, aux, qv, st));    // A (A^* p)
+            }
+            INFFT_TRY(dot(pv, qv, n, part, sc + 2, st));
+            k_cg_alpha<<<1, 1, 0, st>>>(sc);
+            INFFT_LAUNCHED();
+            k_cg_update_xr<<<eb, et, 0, st>>>(x, r, pv, qv, n, sc);
+            INFFT_LAUNCHED();
+            INFFT_TRY(dot(r, r, n, part, sc + 4, st));
+            k_cg_end<<<1, 1, 0, st>>>(sc);
+            INFFT_LAUNCHED();
+            k_cg_keep_best<<<eb, et, 0, st>>>(x, xb, n, sc);
+            INFFT_LAUNCHED();
+            k_cg_update_p<<<eb, et, 0, st>>>(pv, r, n, sc);
+            INFFT_LAUNCHED();
         }
-        INFFT_TRY(dot(pv, qv, n, part, sc + 2, st));
-        k_cg_alpha<<<1, 1, 0, st>>>(sc);
-        INFFT_LAUNCHED();
-        k_cg_update_xr<<<eb, et, 0, st>>>(x, r, pv, qv, n, sc);
-        INFFT_LAUNCHED();
-        INFFT_TRY(dot(r, r, n, part, sc + 4, st));
-        double rr_new = 0;
-        INFFT_TRY(read_back(&rr_new, sc + 4, 8, st));
-        k_cg_beta<<<1, 1, 0, st>>>(sc);
-        INFFT_LAUNCHED();
-        k_cg_update_p<<<eb, et, 0, st>>>(pv, r, n, sc);
-        INFFT_LAUNCHED();
-        INFFT_CUDA(cudaStreamSynchronize(st));
-        if (!(rr_new == rr_new)) { set_error("CG breakdown (NaN)"); return INFFT_ENOTCONV; }
-        if (std::sqrt(rr_new) <= rel_tol * bnorm) { ++it; conv = true; break; }
+        queued += chunk;
+        INFFT_TRY(read_back(state, sc + 10, 3 * 8, st));
+        if (state[1] != 0.0) break;
     }
+    if (state[1] == 2.0) { set_error("CG breakdown (NaN)"); return INFFT_ENOTCONV; }
+    bool conv = state[1] == 1.0;
+    const int it = (int)state[2];
+    x = xb;   // the weights come from the iterate of smallest residual
     // weights in sorted order
     if (second_kind) {
         INFFT_TRY(nfft64(sub, true, x, aux, st));  // A u

@@ -60,12 +60,15 @@ class PointSet:
 class Backend:
     """GPU backend over the library: plans, batched launches, completion events."""
 
-    def __init__(self, weights_iters: int = 30, m: int = 4, sigma: float = 2.0):
+    def __init__(self, weights_iters: int = 30, m: int = 4, sigma: float = 2.0, bopt: bool = False):
+        """bopt: also optimise B (Algorithm 4.3) when a point set is admitted, and serve
+        its reconstructions with B_opt (Algorithm 4.4) instead of the weights (Algorithm 3.7)."""
         import torch
 
         import paper_2302_00414_gb300 as L
         self.torch, self.L = torch, L
-        self.weights_iters, self.m, self.sigma = weights_iters, m, sigma
+        self.weights_iters, self.m, self.sigma, self.bopt = weights_iters, m, sigma, bopt
+        self.mode = L.MODE_BOPT if bopt else L.MODE_DCF
         self._free, self._free_at = 0, -1.0
         self.phase_s = collections.Counter()     # host seconds per build phase
         self.launch_max = collections.Counter()  # longest host time of each launch phase
@@ -81,9 +84,13 @@ class Backend:
         t2 = time.perf_counter()
         p.weights(max_iter=self.weights_iters, rel_tol=1e-12, stream=stream.cuda_stream)
         t3 = time.perf_counter()
+        if self.bopt:
+            p.optimize_B(stream=stream.cuda_stream)
+        t4 = time.perf_counter()
         self.phase_s["points"] += t1 - t0
         self.phase_s["plan"] += t2 - t1
         self.phase_s["weights"] += t3 - t2
+        self.phase_s["bopt"] += t4 - t3
         return p
 
     def plan_bytes(self, plan) -> int:
@@ -93,7 +100,10 @@ class Backend:
         n = ps.N if ps.N else ps.x.shape[0]
         grid = (2 * ps.M) ** ps.d
         cg = 16 * ((4 * ps.M) ** ps.d) * 8   # float64 grids and scratch of the degree-2M solve
-        return 120 * n + 40 * grid + cg
+        extra = 0
+        if self.bopt:   # float64 and plan-precision coefficients, the solve's member lists and V
+            extra = n * (2 * self.m + 2) ** ps.d * (16 + 8 + 8) + 16 * n * ps.d * (2 * self.m + 2)
+        return 120 * n + 40 * grid + cg + extra
 
     def free_bytes(self) -> int:
         # the device query can wait behind another thread's synchronising call (a plan's
@@ -118,7 +128,7 @@ class Backend:
             for f in fs:
                 f.record_stream(stream)
             t1 = time.perf_counter()
-            self.L.adjoint_batched(plans, fs, outs, self.L.MODE_DCF, stream=stream.cuda_stream, slots=slots)
+            self.L.adjoint_batched(plans, fs, outs, self.mode, stream=stream.cuda_stream, slots=slots)
             t2 = time.perf_counter()
             ev = torch.cuda.Event()
             ev.record(stream)

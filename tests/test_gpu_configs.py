@@ -75,3 +75,34 @@ def test_batched_graph_large_sets():
     torch.cuda.synchronize()
     for i, (M, x) in enumerate(sets):
         assert sampled_parity(x, ws[i], fh[i], M, 2, hs[i].cpu().numpy(), 128, 500 + i) < 1e-5
+
+
+def test_graph_batch_over_pinned_host_buffers():
+    """A graph batch whose samples and results live in page-locked host memory holds the
+    copies too: every replay gives the device-buffer result bit for bit; pageable host
+    buffers are refused."""
+    L, torch = lib_or_skip()
+    sets = inputs.batch_sets(5, 31)
+    plans, fd, hd, fh, hh = [], [], [], [], []
+    for i, (M, x) in enumerate(sets):
+        p = L.Plan(x, M, 2.0, 4, "fp32")
+        p.set_weights(inputs.coeffs_complex((x.shape[0],), 40 + i) / x.shape[0])
+        plans.append(p)
+        f = torch.from_numpy(inputs.samples_complex(x.shape[0], 50 + i).astype(np.complex64))
+        fd.append(f.cuda())
+        hd.append(torch.empty((M, M), dtype=torch.complex64, device="cuda"))
+        fh.append(f.pin_memory())
+        hh.append(torch.zeros((M, M), dtype=torch.complex64).pin_memory())
+    L.Batch(plans, fd, hd, L.MODE_DCF).run()
+    torch.cuda.synchronize()
+    hb = L.Batch(plans, [t.numpy() for t in fh], [t.numpy() for t in hh], L.MODE_DCF)
+    for rep in range(3):
+        for t in hh:
+            t.zero_()
+        hb.run()
+        torch.cuda.synchronize()
+        for a, b in zip(hh, hd):
+            assert np.array_equal(a.numpy(), b.cpu().numpy())
+    pageable = [np.zeros((M, M), dtype=np.complex64) for M, _ in sets]
+    with pytest.raises(L.InfftError):
+        L.Batch(plans, [t.numpy() for t in fh], pageable, L.MODE_DCF)

@@ -279,3 +279,96 @@ def test_fp32_d2_tiny_point_counts(N):
     assert p.work_items == 1
     h = p.adjoint(to_dev(torch, f, torch.complex64)).cpu().numpy()
     assert rel(h, NF.adjoint_nfft(x, f, M, sigma, m)) < 1e-5
+
+
+@pytest.mark.parametrize("M,prec,mode", [
+    (32, "fp32", "plain"),     # Ms = 64: one CTA per job
+    (64, "fp32", "dcf"),       # Ms = 128: clusters of 2
+    (128, "fp32", "plain"),    # Ms = 256: clusters of 8
+    (256, "fp32", "dcf"),      # Ms = 512: clusters of 16
+    (128, "fp64", "plain"),    # float64 Ms = 256: clusters of 8
+    (256, "fp64", "plain"),    # float64 Ms = 512: the two-kernel form
+    (32, "fp32", "bopt"),      # B_opt tiles (edge T + 2m + 1)
+])
+def test_fused_merge_fft_matches_two_kernel_form(monkeypatch, M, prec, mode):
+    """The cluster kernel that fuses the halo merge with both FFT passes (Algorithm 2.4
+    steps 2-3) gives the two-kernel form's result to rounding (the cells' contributions
+    are summed in another fixed order), the oracle's Algorithm 2.4 / 4.4, and the same
+    result in a batch as alone."""
+    L, torch = lib_or_skip()
+    from oracle import bopt as BO
+    N = 3 * M * M if mode != "bopt" else 2 * M * M
+    x = inputs.random_points(N, 2, 500 + M)
+    f = inputs.samples_complex(N, 501 + M)
+    cd = torch.complex64 if prec == "fp32" else torch.complex128
+    m = 4 if mode != "bopt" else 3
+    p = L.Plan(x, M, 2.0, m, prec)
+    md, c = L.MODE_PLAIN, f
+    if mode == "dcf":
+        w = inputs.coeffs_complex((N,), 7) / N
+        p.set_weights(w)
+        md, c = L.MODE_DCF, w * f
+    coef = None
+    if mode == "bopt":
+        p.optimize_B()
+        coef = p.get_bopt()
+        md = L.MODE_BOPT
+    fd = to_dev(torch, f, cd)
+    out = {}
+    for form in ("0", "1"):
+        monkeypatch.setenv("INFFT_FUSED_MERGE_FFT", form)
+        out[form] = p.adjoint(fd, mode=md).cpu().numpy().ravel()
+    tol = 1e-6 if prec == "fp32" else 1e-14
+    assert rel(out["1"], out["0"]) < tol
+    if mode == "bopt":
+        ref = BO.reconstruct(x, f, coef, M, 2.0, m, "kb", BO.PATTERN_2M2)
+    else:
+        ref = NF.adjoint_nfft(x, c, M, 2.0, m)
+    assert rel(out["1"], ref) < (1e-5 if prec == "fp32" else 1e-12)
+    # alone and in a batch with another set: bit for bit
+    monkeypatch.setenv("INFFT_FUSED_MERGE_FFT", "1")
+    q = L.Plan(inputs.random_points(5000, 2, 9), M, 2.0, m, prec)
+    if mode == "dcf":
+        q.set_weights(np.ones(5000) / 5000)
+    if mode == "bopt":
+        q.optimize_B()
+    g = to_dev(torch, inputs.samples_complex(5000, 10), cd)
+    h1 = torch.empty((M, M), dtype=cd, device="cuda")
+    h2 = torch.empty((M, M), dtype=cd, device="cuda")
+    L.adjoint_batched([q, p], [g, fd], [h1, h2], md)
+    assert np.array_equal(h2.cpu().numpy().ravel(), out["1"])
+
+
+@pytest.mark.parametrize("tune", [
+    {"tile": 8}, {"item_cap": 64}, {"item_cap": 1024}, {"prefetch": 1}, {"prefetch": 2},
+    {"fused_fft": 1}, {"fused_fft": 2}, {"branches": 1}, {"branches": 6},
+    {"tile": 8, "item_cap": 100, "prefetch": 2, "fused_fft": 1, "branches": 2},
+])
+def test_tuned_plans_give_the_same_reconstruction(tune):
+    """Kernel choices (infft_tune_t) change speed only: a batch of DCF reconstructions with
+    them equals the default to float32 rounding and the oracle's Algorithm 2.4."""
+    L, torch = lib_or_skip()
+    sets = [(M, inputs.random_points(3 * M * M, 2, 700 + M)) for M in (32, 64, 128)]
+    outs = {}
+    for key, tn in (("default", None), ("tuned", tune)):
+        plans, fs, hs = [], [], []
+        for i, (M, x) in enumerate(sets):
+            p = L.Plan(x, M, 2.0, 4, "fp32", tune=tn)
+            p.set_weights(np.full(x.shape[0], 1.0 / x.shape[0]))
+            plans.append(p)
+            fs.append(to_dev(torch, inputs.samples_complex(x.shape[0], 710 + i), torch.complex64))
+            hs.append(torch.empty((M, M), dtype=torch.complex64, device="cuda"))
+        L.adjoint_batched(plans, fs, hs, L.MODE_DCF)
+        outs[key] = [h.cpu().numpy().ravel() for h in hs]
+    for i, (M, x) in enumerate(sets):
+        assert rel(outs["tuned"][i], outs["default"][i]) < 1e-6
+        f = inputs.samples_complex(x.shape[0], 710 + i).astype(np.complex64).astype(np.complex128)
+        assert rel(outs["tuned"][i], NF.adjoint_nfft(x, f / x.shape[0], M, 2.0, 4)) < 1e-5
+
+
+def test_invalid_tuning_is_rejected():
+    L, torch = lib_or_skip()
+    x = inputs.random_points(100, 2, 1)
+    for tn in ({"tile": 12}, {"tile": 4}, {"branches": 9}, {"prefetch": 3}, {"item_cap": -1}):
+        with pytest.raises(L.InfftError):
+            L.Plan(x, 16, 2.0, 4, "fp32", tune=tn)

@@ -126,3 +126,25 @@ def test_dcf_with_given_weights_matches_exact_sum(prec, tol):
     h = p.adjoint(to_dev(torch, f, cd), mode=L.MODE_DCF).cpu().numpy()
     ref = WT.reconstruct_exact(x, f, w, M)
     assert rel(h, ref) < (tol if prec == "fp32" else 1e-9)
+
+
+def test_capped_cg_returns_its_best_iterate():
+    """A capped CG on a badly conditioned grid (polar, Section 5): the weights come from the
+    iterate of smallest residual among x_1, x_2, ..., so in the second kind (where the CG
+    residual e_0 - A^* A u is -conj(A^T w - e_0)) the 2-norm of A_2M^T w - e_0 never grows as
+    max_iter grows, while the last iterate's residual oscillates."""
+    L, torch = lib_or_skip()
+    x = inputs.polar(128, 64)           # N = 8192 >= |I_2M| = 4096 for M = 32
+    p = L.Plan(x, 32, 2.0, 4, "fp32")
+    e0 = (np.arange(64 * 64) == (32 * 64 + 32)).astype(float)
+    prev = np.inf
+    for it in (1, 2, 3, 5, 8, 13, 21, 30):
+        info = p.weights(max_iter=it, rel_tol=1e-14)
+        assert info["status"] in (L.OK, L.ENOTCONV)
+        assert info["iters"] <= it
+        w = p.get_weights()
+        assert np.all(np.isfinite(w)) and np.any(w != 0)
+        r2 = float(np.linalg.norm(FO.transpose_apply(x, w, 64) - e0))
+        assert r2 <= prev * (1 + 1e-9) + 1e-12
+        assert abs(info["residual_inf"] - np.max(np.abs(FO.transpose_apply(x, w, 64) - e0))) < 1e-6 * max(1, r2)
+        prev = r2
