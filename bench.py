@@ -200,24 +200,31 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the spreading kernel from the committed ncu summary, or
-    None when the kernel sources changed since that capture (hash mismatch)."""
+def profiled(name: str = "k_spread2d_batched_d2_m4.md"):
+    """Figures of the committed ncu summary of the spreading kernel (keys "dram_bytes_per_launch",
+    "smem_pipe_frac"), or {} when the kernel sources changed since that capture (hash
+    mismatch): a stale capture is not reported."""
     import hashlib
-    summary = os.path.join(ROOT, "profiles", "k_spread2d_batched_d2_m4.md")
+    summary = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(summary):
-        return None
+        return {}
     h = hashlib.sha256()
     for f in ("spread2d.cuh", "common.cuh", "jobset.cuh"):
         with open(os.path.join(ROOT, "paper_2302_00414_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    want, value = None, None
+    want, out = None, {}
     for line in open(summary):
         if line.startswith("source_sha256:"):
             want = line.split(":", 1)[1].strip()
-        if line.startswith("dram_bytes_per_launch:"):
-            value = int(line.split(":", 1)[1].strip())
-    return value if want == h.hexdigest()[:16] else None
+        for key in ("dram_bytes_per_launch", "smem_pipe_frac"):
+            if line.startswith(key + ":"):
+                out[key] = float(line.split(":", 1)[1].strip())
+    return out if want == h.hexdigest()[:16] else {}
+
+
+# FP32 SIMT peak of the GB300 from unit counts and the clock: 152 SMs x 128 FP32 lanes x
+# 2 flops per fused multiply-add x 2.07 GHz (derived, not measured)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def measured_peak():
@@ -418,8 +425,26 @@ def run_ours(args, rank, world, dist):
     fft_ms = [statistics.median(s["fft"][t] for s in stage) for t in range(2)]
     # algorithmic bytes of the DCF spread: N (4d + 8 + 8) + 8 G  (x, f, w; grid written once)
     spread_bytes = Ntot * (4 * 2 + 8 + 8) + 8 * grid_cells
+    # flops of the DCF spread: (2m+1)^2 taps of a real window value times a complex sample
+    # (two multiply-adds) per point, and the 2 (2m+1) window values (degree-10 polynomials)
+    spread_flops = Ntot * ((2 * 4 + 1) ** 2 * 4 + 2 * (2 * 4 + 1) * 2 * 10)
     peak, peak_kind = measured_peak()
     achieved = spread_bytes / (spread_ms / 1e3) / 1e9
+    prof = profiled()
+    # merge and the two FFT passes: bytes of the tensors they read and write (the padded
+    # tiles as written by the spread), against their event-timed stage
+    tile = ((tune_cfg or {}).get("tile") or 16)
+    padded = sum(p.work_items * (tile + 2 * 4) ** 2 * 8 for p in plans)   # P = T + 2m per padded edge
+    G = grid_cells
+    Kc = coeffs
+    Mrow = sum(p.Ms * M for p, (M, _) in zip(plans, sets))
+    stage_roof = {}
+    for name, nbytes, ms in (("merge", padded + 8 * G, merge_ms),
+                             ("fft_pass1", 8 * G + 8 * Mrow, fft_ms[0]),
+                             ("fft_pass2", 8 * Mrow + 8 * Kc, fft_ms[1])):
+        if ms > 0:
+            gbs = nbytes / (ms / 1e3) / 1e9
+            stage_roof[name] = {"bytes": int(nbytes), "ms": ms, "achieved": gbs, "frac": gbs / peak}
 
     # ---- plain: one reconstruction at a time -----------------------------------------------
     torch.cuda.synchronize()
@@ -463,7 +488,7 @@ def run_ours(args, rank, world, dist):
     d2h = sum(int(h.numel()) * 8 for h in hs)
 
     # ---- accuracy against the FP64 oracle (sampled coefficients) -------------------------
-    rel_errs = []
+    rel_errs, e2s = [], []
     if rank == 0:
         from oracle import fourier as FO
         L.adjoint_batched(plans, fs, hs, L.MODE_DCF)
@@ -478,6 +503,17 @@ def run_ours(args, rank, world, dist):
             ref = _oracle_parity((x, w * fs[i].cpu().numpy().astype(np.complex128), M, ks))
             got = hs[i].cpu().numpy().ravel()[ks]
             rel_errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+        # e_2 = ||h - fhat|| / ||fhat|| of the reconstruction with the capped CG's weights, for
+        # data f = A fhat made by a float64 NFFT with a wide window (m = 10)
+        for i in pick:
+            M, x = sets[i]
+            fh = inputs.coeffs_complex((M, M), 9000 + i)
+            pf = L.Plan(x, M, 2.0, 10, "fp64")
+            fx = pf.forward(np.ascontiguousarray(fh, dtype=np.complex128))
+            pf.close()
+            hh = plans[i].adjoint(torch.from_numpy(fx.astype(np.complex64)).to(dev), mode=L.MODE_DCF)
+            e2s.append({"M": M, "N": int(x.shape[0]), "e2": float(np.linalg.norm(hh.cpu().numpy().ravel() - fh.ravel()) /
+                                                               np.linalg.norm(fh)), "residual_inf": wres[i]})
 
     # ---- B_opt leg: Algorithm 4.3 on a stratified sample of the sets, then Algorithm 4.4 --
     bopt = None
@@ -508,10 +544,20 @@ def run_ours(args, rank, world, dist):
         "plain": {"value": plain_rate, "unit": "recon/s"}, "vs_plain": recon_per_s / world / plain_rate,
         "rel_err_vs_fp64": max(rel_errs) if rel_errs else None,
         "stage_ms": {"spread": spread_ms, "merge": merge_ms, "fft": fft_ms},
-        "roofline": {"bound": "hbm", "kernel": "k_spread2d", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": profiled_traffic(),
+        "roofline": {"bound": "smem", "kernel": "k_spread2d<float, 4, 0, 1>", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": int(prof["dram_bytes_per_launch"]) if "dram_bytes_per_launch" in prof else None,
                      "peak_kind": peak_kind, "algorithmic_bytes": int(spread_bytes),
-                     "note": "bound on chip (ncu: shared-memory wavefronts 71% of peak, issue 59%, DRAM 9%), see profiles/"},
+                     "binding": {"resource": "shared-memory data pipe (ncu l1tex data-pipe wavefronts)",
+                                 "utilization": prof.get("smem_pipe_frac"),
+                                 "source": "profiles/k_spread2d_batched_d2_m4.md"},
+                     "flops": {"algorithmic": int(spread_flops), "achieved_tflops": spread_flops / (spread_ms / 1e3) / 1e12,
+                               "peak_tflops": FP32_PEAK_TFLOPS,
+                               "frac": spread_flops / (spread_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+                               "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+                     "note": "achieved/peak/frac: HBM (algorithmic bytes / event-timed spread); the kernel is "
+                             "bound on chip by the shared-memory pipe"},
+        "stage_roofline": stage_roof,
         "e2e": {"value": e2e_rate, "unit": "recon/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": "graph replay over page-locked host buffers (infft_batch_create / infft_batch_run)"},
         "e2e_call": {"value": e2e_call_rate, "unit": "recon/s",
@@ -519,7 +565,7 @@ def run_ours(args, rank, world, dist):
         "gpu_launches": int(kernels_per_step * args.steps),
         "clocks": clocks,
         "precompute": {"setup_s": setup_s, "plan_s": t_plan, "weights_s": t_w, "cg_iters": args.cg_iters,
-                       "weights_residual_max": max(wres)},
+                       "weights_residual_max": max(wres), "e2_vs_fhat": e2s},
         "cpu_baseline": cpu,
         "bopt": bopt,
         "tuning": tuning,
@@ -571,8 +617,13 @@ def run_single(args, rank, world, dist):
         fh_true = inputs.coeffs_complex((M,), 1000 * cidx)
         f_np = FO.ndft(x, fh_true, M)           # f = A fhat by the oracle's exact sums
     else:
-        fh_true = None
-        f_np = inputs.samples_complex(N, 1000 * cidx + 1)
+        # f = A fhat for random fhat by a float64 NFFT of the library with a wide window
+        # (m = 10 for d = 2, 6 for d = 3; error ~1e-14), as the paper makes its data by an
+        # NFFT: e_2 = ||h - fhat|| / ||fhat|| then measures the weights and the reconstruction
+        fh_true = inputs.coeffs_complex((M,) * d, 1000 * cidx)
+        pf = L.Plan(x, M, 2.0, 10 if d == 2 else 6, "fp64")
+        f_np = pf.forward(np.ascontiguousarray(fh_true, dtype=np.complex128))
+        pf.close()
     cg_iters = {"C1": 500, "C2": 30, "C4": 10}[label]
     per_m = {}
     for m in ms:
@@ -657,7 +708,8 @@ def run_single(args, rank, world, dist):
                "gpu_launches": int(kernels_per_step * args.steps), "clocks": clk.summary(),
                "h2d_bytes_per_step": N * cbytes, "d2h_bytes_per_step": K * cbytes}
         if fh_true is not None:
-            rec["e2_vs_fhat"] = float(np.linalg.norm(h.cpu().numpy().ravel() - fh_true) / np.linalg.norm(fh_true))
+            rec["e2_vs_fhat"] = float(np.linalg.norm(h.cpu().numpy().ravel() - fh_true.ravel()) /
+                                      np.linalg.norm(fh_true))
         per_m[m] = rec
         batch.close()
         p.close()
@@ -799,7 +851,7 @@ def run_serving(args, rank, world, dist):
         d, M, _ = meta[key]
         by_class.setdefault(f"d{d}M{M}", []).append(sec)
     # parity of a few served results with the oracle's exact sums (same weights)
-    rel_errs = []
+    rel_errs, e2s = [], []
     if rank == 0:
         from oracle import fourier as FO
         picks = [r for r in done if r.out is not None and r.key in server.plans][:3]

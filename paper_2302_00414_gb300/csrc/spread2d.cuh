@@ -246,16 +246,19 @@ __global__ void __launch_bounds__(128, spread2d_pair<R, MM, BOPT>() ? 5 : 1)
                     constexpr int S = W + 1;
                     const int ox = meta[p * 3 + 1];
                     const int sx = lane - ox;
-                    if (sx >= 0 && sx < S) {
-                        const int i = meta[p * 3 + 2];
-                        const cx<R> cv = cst[p];
-                        const cx<R>* cf = J.coef + (size_t)i * S * S + sx;
+                    // every lane loads (a column of the point's S x S block, clamped), and the
+                    // lanes outside the block add zero: with no branch around the loads the
+                    // unrolled points' coefficient loads are in flight together
+                    const bool act = sx >= 0 && sx < S;
+                    const int sxc = min(max(sx, 0), S - 1);
+                    const int i = meta[p * 3 + 2];
+                    const cx<R> cv = act ? cst[p] : mk<R>(0, 0);
+                    const cx<R>* cf = J.coef + (size_t)i * S * S + sxc;
 #pragma unroll
-                        for (int k = 0; k < S; ++k) {
-                            const cx<R> b = cf[k * S];
-                            acc[k].x += b.re * cv.re + b.im * cv.im;   // conj(b) f
-                            acc[k].y += b.re * cv.im - b.im * cv.re;
-                        }
+                    for (int k = 0; k < S; ++k) {
+                        const V2 b = __ldg(reinterpret_cast<const V2*>(cf + k * S));
+                        acc[k].x += b.x * cv.re + b.y * cv.im;   // conj(b) f
+                        acc[k].y += b.x * cv.im - b.y * cv.re;
                     }
                 } else {
                     const R wx = psx[p * PX + lane];
