@@ -318,7 +318,8 @@ infft_status infft_adjoint_batched_slots(const infft_plan_t* plans, int count, i
  * infft_adjoint_batched_timed -- as infft_adjoint_batched (count <= 96), and
  * reports device times of the stages in stage_ms[5]: spreading, halo merge and
  * the FFT passes along each axis (unused entries 0), from CUDA events recorded on
- * `stream` between the kernel launches.  Synchronises.
+ * `stream` between the kernel launches.  Jobs whose plans turn on the fused merge-FFT
+ * kernel (infft_tune_t fused_fft) count it in the merge stage.  Synchronises.
  */
 infft_status infft_adjoint_batched_timed(const infft_plan_t* plans, int count, int mode,
                                          const void* const* f, void* const* fhat, void* stream,

@@ -443,24 +443,35 @@ static infft_status optimize_impl(infft_plan_s* p, unsigned opts, double* max_re
         else { big.push_back((int)c); n_big = std::max(n_big, n); }
     }
     std::stable_sort(big.begin(), big.end(), [&](int a, int b) { return hs[a + 1] - hs[a] > hs[b + 1] - hs[b]; });
+    // The solve goes out in short launches (about two columns per block each), so that the
+    // blocks leave the SMs every few milliseconds and work of higher-priority streams (a
+    // server's reconstructions while a new point set is admitted) is scheduled in between;
+    // each launch has its own work counter.
     int* list = (int*)alloc((small.size() + big.size()) * 4);
-    int* next = (int*)alloc(2 * 4);
-    if (!list || !next) { set_error("optimize_B: out of device memory (column lists)"); return INFFT_ENOMEM; }
+    if (!list) { set_error("optimize_B: out of device memory (column lists)"); return INFFT_ENOMEM; }
     if (!small.empty())
         INFFT_CUDA(cudaMemcpyAsync(list, small.data(), small.size() * 4, cudaMemcpyHostToDevice, st));
     if (!big.empty())
         INFFT_CUDA(cudaMemcpyAsync(list + small.size(), big.data(), big.size() * 4, cudaMemcpyHostToDevice, st));
-    INFFT_CUDA(cudaMemsetAsync(next, 0, 2 * 4, st));
     if (!small.empty()) {
         const size_t smem = bopt_fixed_bytes(std::max(n_small, 1), g.d) + (size_t)tri(n_small + 1, 0) * 16 + 64;
         int per_sm = 0;
         INFFT_CUDA(cudaFuncSetAttribute(k_bopt_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         INFFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bopt_solve, BOPT_THREADS, smem));
         const int blocks = nsm * std::max(1, per_sm);
-        k_bopt_solve<<<blocks, BOPT_THREADS, smem, st>>>(g, start, members, p->x64, V, rhs2, list, (int)small.size(),
-                                                          next, n_small, std::max(n_small, 1), nullptr, 1, nullptr,
-                                                          (cx<double>*)p->coef64, eps, status);
-        INFFT_LAUNCHED();
+        const long long chunk = 2LL * blocks;
+        const long long nchunk = ((long long)small.size() + chunk - 1) / chunk;
+        int* next = (int*)alloc((size_t)nchunk * 4);   // one work counter per launch
+        if (!next) { set_error("optimize_B: out of device memory (work counters)"); return INFFT_ENOMEM; }
+        INFFT_CUDA(cudaMemsetAsync(next, 0, (size_t)nchunk * 4, st));
+        for (long long c = 0; c < nchunk; ++c) {
+            const long long c0 = c * chunk;
+            const int n = (int)std::min<long long>(chunk, (long long)small.size() - c0);
+            k_bopt_solve<<<std::min(blocks, n), BOPT_THREADS, smem, st>>>(
+                g, start, members, p->x64, V, rhs2, list + c0, n, next + c, n_small, std::max(n_small, 1), nullptr, 1,
+                nullptr, (cx<double>*)p->coef64, eps, status);
+            INFFT_LAUNCHED();
+        }
     }
     if (!big.empty()) {
         const bool fix_smem = bopt_fixed_bytes(n_big, g.d) + 64 <= cap;
@@ -482,10 +493,19 @@ static infft_status optimize_impl(infft_plan_s* p, unsigned opts, double* max_re
         }
         const size_t smem = (fix_smem ? bopt_fixed_bytes(n_big, g.d) : 0) + 16 + 64;
         INFFT_CUDA(cudaFuncSetAttribute(k_bopt_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_bopt_solve<<<blocks, BOPT_THREADS, smem, st>>>(g, start, members, p->x64, V, rhs2, list + small.size(),
-                                                          (int)big.size(), next + 1, 0, n_big, gscr, fix_smem ? 1 : 0,
-                                                          gfix, (cx<double>*)p->coef64, eps, status);
-        INFFT_LAUNCHED();
+        // one column per block per launch (largest first)
+        const size_t nchunk = (big.size() + (size_t)blocks - 1) / (size_t)blocks;
+        int* next = (int*)alloc(nchunk * 4);   // one work counter per launch
+        if (!next) { set_error("optimize_B: out of device memory (work counters)"); return INFFT_ENOMEM; }
+        INFFT_CUDA(cudaMemsetAsync(next, 0, nchunk * 4, st));
+        for (size_t c = 0; c < nchunk; ++c) {
+            const size_t c0 = c * (size_t)blocks;
+            const int n = (int)std::min<size_t>((size_t)blocks, big.size() - c0);
+            k_bopt_solve<<<n, BOPT_THREADS, smem, st>>>(g, start, members, p->x64, V, rhs2, list + small.size() + c0, n,
+                                                         next + c, 0, n_big, gscr, fix_smem ? 1 : 0, gfix,
+                                                         (cx<double>*)p->coef64, eps, status);
+            INFFT_LAUNCHED();
+        }
     }
     const int cb = (int)std::min<long long>((nent + 255) / 256, 65535LL * 16);
     if (p->fp64) k_bopt_convert<double><<<cb, 256, 0, st>>>((cx<double>*)p->coef64, nent, (cx<double>*)p->coef);

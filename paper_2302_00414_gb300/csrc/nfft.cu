@@ -293,6 +293,16 @@ __device__ __forceinline__ cx<R> merged_cell(const Job<R>& J, long long cidx) {
 // so that the bit-reversed scatter and the short butterfly strides spread over banks.
 __device__ __forceinline__ int skew(int i) { return i + (i >> 4); }
 
+// lines of length n per FFT block: a 16 KB budget of complex elements, at most 32 lines (more,
+// smaller blocks hide the passes' load latency better: batched d = 2, n = 512: 64 / 32 / 16 / 8 KB
+// of lines per block gave FFT passes of 0.140 / 0.109 / 0.100 / 0.104 ms).  Per job, so that the
+// blocks of small grids are as full as those of large ones.
+__host__ __device__ inline int fft_lines(int n, int elem) {
+    int L = 1;
+    while (L < 32 && 2 * L * n * elem <= 16 * 1024) L *= 2;
+    return L;
+}
+
 template <class R, int D, bool FWD>
 __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> js, int pass) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -301,7 +311,7 @@ __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> j
     const int jb = find_job(js.pre_fft[pass], js.njobs, gblk);
     const Job<R>& J = js.job[jb];
     const int lb = gblk - js.pre_fft[pass][jb];
-    const int Ms = J.Ms, M = J.M, L = js.L;
+    const int Ms = J.Ms, M = J.M, L = fft_lines(J.Ms, (int)sizeof(cx<R>));
     const int t = FWD ? pass : D - 1 - pass;
     const bool expl = !FWD && js.axA > 0;   // one explicit pass over an (A, Ms, B) tensor
     const long long A = expl ? js.axA : ipow(Ms, t);
@@ -349,12 +359,29 @@ __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> j
     __syncthreads();
 
     if (!FWD) {
-        for (int e = tid; e < L * n; e += nth) {
-            int l, i;
-            if (lanes_b) { l = e & (L - 1); i = e >> logL; } else { i = e & (n - 1); l = e >> logn; }
-            const long long g0 = s_in[l];
-            const cx<R> v = (g0 >= 0) ? src[g0 + (long long)i * B] : mk<R>(0, 0);
-            buf[l * ns + skew(bitrev(i, logn))] = v;
+        // each thread issues the loads of up to eight elements before storing any, so that
+        // the block waits for one global-load latency rather than eight in a row
+        constexpr int KL = 8;
+        const int total = L * n;
+        for (int e0 = tid; e0 < total; e0 += KL * nth) {
+            cx<R> v[KL];
+            int pos[KL];
+#pragma unroll
+            for (int k = 0; k < KL; ++k) {
+                const int e = e0 + k * nth;
+                pos[k] = -1;
+                v[k] = mk<R>(0, 0);
+                if (e < total) {
+                    int l, i;
+                    if (lanes_b) { l = e & (L - 1); i = e >> logL; } else { i = e & (n - 1); l = e >> logn; }
+                    const long long g0 = s_in[l];
+                    pos[k] = l * ns + skew(bitrev(i, logn));
+                    if (g0 >= 0) v[k] = src[g0 + (long long)i * B];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < KL; ++k)
+                if (pos[k] >= 0) buf[pos[k]] = v[k];
         }
     } else {
         for (int e = tid; e < L * ns; e += nth) buf[e] = mk<R>(0, 0);
@@ -532,14 +559,18 @@ __global__ void __launch_bounds__(128) k_interp(const __grid_constant__ JobSet<R
 // ---------------------------------------------------------------------------------------
 // host drivers
 
-// lines per FFT block: more, smaller blocks hide the passes' load latency better (batched
-// d = 2, n = 512: 64 / 32 / 16 / 8 KB of lines per block give FFT passes of 0.140 / 0.109 /
-// 0.100 / 0.104 ms)
-static int pick_lines(int n, size_t elem) {
-    const size_t budget = 16 * 1024;
-    int L = 1;
-    while (L < 32 && (size_t)(2 * L) * n * elem <= budget) L *= 2;
-    return L;
+static int pick_lines(int n, size_t elem) { return fft_lines(n, (int)elem); }
+
+// shared memory of an FFT launch over the jobs of js: the largest of the jobs' line buffers
+// plus twiddles
+template <class R>
+static size_t fft_smem(const JobSet<R>& js) {
+    size_t mx = 0;
+    for (int j = 0; j < js.njobs; ++j) {
+        const int n = js.job[j].Ms, L = pick_lines(n, sizeof(cx<R>));
+        mx = std::max(mx, ((size_t)L * (n + n / 16) + n / 2) * sizeof(cx<R>));
+    }
+    return mx;
 }
 
 template <class R>
@@ -560,7 +591,8 @@ static void fill_prefixes(JobSet<R>& js, int D, bool forward) {
             if (p < D) {
                 const int t = forward ? p : D - 1 - p;
                 const long long lines = (long long)ipow(J.Ms, t) * ipow(J.M, D - 1 - t);
-                blocks = (int)((lines + js.L - 1) / js.L);
+                const int Lj = pick_lines(J.Ms, sizeof(cx<R>));
+                blocks = (int)((lines + Lj - 1) / Lj);
             }
             js.pre_fft[p][j + 1] = js.pre_fft[p][j] + blocks;
         }
@@ -594,9 +626,7 @@ static JobSet<R>* new_subset(const JobSet<R>& js, const std::vector<int>& idx) {
 // pruned FFT passes with deconvolution, common to every spreading variant
 template <class R, int D>
 static infft_status launch_fft_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* ev) {
-    int maxMs = 0;
-    for (int j = 0; j < js.njobs; ++j) maxMs = std::max(maxMs, js.job[j].Ms);
-    const size_t fsmem = ((size_t)js.L * (maxMs + maxMs / 16) + maxMs / 2) * sizeof(cx<R>);
+    const size_t fsmem = fft_smem(js);
     INFFT_CUDA(cudaFuncSetAttribute(k_fft<R, D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
     for (int p = 0; p < D; ++p) {
         k_fft<R, D, false><<<js.pre_fft[p][js.njobs], 256, fsmem, st>>>(js, p);
@@ -678,9 +708,7 @@ static infft_status launch_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* 
 template <class R, int D>
 static infft_status launch_forward(JobSet<R>& js, cudaStream_t st) {
     fill_prefixes(js, D, true);
-    int maxMs = 0;
-    for (int j = 0; j < js.njobs; ++j) maxMs = std::max(maxMs, js.job[j].Ms);
-    const size_t fsmem = ((size_t)js.L * (maxMs + maxMs / 16) + maxMs / 2) * sizeof(cx<R>);
+    const size_t fsmem = fft_smem(js);
     INFFT_CUDA(cudaFuncSetAttribute(k_fft<R, D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
     for (int p = 0; p < D; ++p) {
         k_fft<R, D, true><<<js.pre_fft[p][js.njobs], 256, fsmem, st>>>(js, p);
@@ -745,7 +773,7 @@ template <class R, int D>
 static infft_status fft_passes_d(JobSet<R>& js, cudaStream_t st, bool forward) {
     fill_prefixes(js, D, forward);
     const int n = js.job[0].Ms;
-    const size_t fsmem = ((size_t)js.L * (n + n / 16) + n / 2) * sizeof(cx<R>);
+    const size_t fsmem = fft_smem(js);
     if (forward) {
         INFFT_CUDA(cudaFuncSetAttribute(k_fft<R, D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
         for (int p = 0; p < D; ++p) {
@@ -792,7 +820,7 @@ infft_status run_fft_axis(const Job<R>& J, long long A, long long B, int nblk, c
         return INFFT_EUNSUPPORTED;
     }
     js.pre_fft[0][1] = (int)((lines + js.L - 1) / js.L);
-    const size_t fsmem = ((size_t)js.L * (n + n / 16) + n / 2) * sizeof(cx<R>);
+    const size_t fsmem = fft_smem(js);
     INFFT_CUDA(cudaFuncSetAttribute(k_fft<R, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
     k_fft<R, 2, false><<<js.pre_fft[0][1], 256, fsmem, st>>>(js, 0);
     INFFT_LAUNCHED();

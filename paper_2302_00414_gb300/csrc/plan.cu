@@ -894,7 +894,34 @@ struct BranchSet {
     int dev = -1, prio = 0;
     cudaStream_t s[8] = {};
     cudaEvent_t e[9] = {};
+    cudaStream_t cs = nullptr;     // host-input copies
+    cudaEvent_t r[9] = {};         // a branch's inputs have arrived; r[8]: all copies issued
 };
+
+// Host inputs of a branched batch are copied to the plans' I/O buffers on one copy stream in
+// branch order, the smallest branch first, each branch waiting for its own copies only: the
+// first branches start computing while the later ones' samples are still arriving (copying
+// every branch's inputs at once delayed all of them).  fin[i] becomes the device input of
+// job i.  The copy stream is joined back into st.
+static infft_status stage_inputs(const infft_plan_t* plans, const std::vector<std::vector<int>>& grp,
+                                 const void* const* f, std::vector<const void*>& fin, cudaStream_t st,
+                                 cudaStream_t cs, cudaEvent_t fork, const cudaEvent_t* ready, cudaEvent_t done,
+                                 const cudaStream_t* br) {
+    INFFT_CUDA(cudaStreamWaitEvent(cs, fork, 0));
+    for (size_t g = 0; g < grp.size(); ++g) {
+        for (int i : grp[g]) {
+            if (is_device_pointer(f[i])) continue;
+            const size_t C = plans[i]->fp64 ? 16 : 8;
+            INFFT_CUDA(cudaMemcpyAsync(plans[i]->io_in, f[i], (size_t)plans[i]->N * C, cudaMemcpyHostToDevice, cs));
+            fin[i] = plans[i]->io_in;
+        }
+        INFFT_CUDA(cudaEventRecord(ready[g], cs));
+        INFFT_CUDA(cudaStreamWaitEvent(br[g], ready[g], 0));
+    }
+    INFFT_CUDA(cudaEventRecord(done, cs));
+    INFFT_CUDA(cudaStreamWaitEvent(st, done, 0));
+    return INFFT_OK;
+}
 
 static infft_status branch_set(cudaStream_t st, BranchSet** out) {
     static thread_local std::vector<BranchSet> sets;
@@ -908,6 +935,8 @@ static infft_status branch_set(cudaStream_t st, BranchSet** out) {
     b.prio = prio;
     for (int g = 0; g < 8; ++g) INFFT_CUDA(cudaStreamCreateWithPriority(&b.s[g], cudaStreamNonBlocking, prio));
     for (int g = 0; g < 9; ++g) INFFT_CUDA(cudaEventCreateWithFlags(&b.e[g], cudaEventDisableTiming));
+    INFFT_CUDA(cudaStreamCreateWithPriority(&b.cs, cudaStreamNonBlocking, prio));
+    for (int g = 0; g < 9; ++g) INFFT_CUDA(cudaEventCreateWithFlags(&b.r[g], cudaEventDisableTiming));
     sets.push_back(b);
     *out = &sets.back();
     return INFFT_OK;
@@ -929,14 +958,16 @@ static infft_status run_branched(const infft_plan_t* plans, int count, int mode,
     INFFT_TRY(branch_set(st, &b));
     const std::vector<std::vector<int>> grp = split_groups(plans, count, G);
     INFFT_CUDA(cudaEventRecord(b->e[8], st));
+    for (int g = 0; g < G; ++g) INFFT_CUDA(cudaStreamWaitEvent(b->s[g], b->e[8], 0));
+    std::vector<const void*> fin(f, f + count);
+    if (host_in) INFFT_TRY(stage_inputs(plans, grp, f, fin, st, b->cs, b->e[8], b->r, b->r[8], b->s));
     infft_status s = INFFT_OK;
     for (int g = 0; g < G; ++g) {
-        INFFT_CUDA(cudaStreamWaitEvent(b->s[g], b->e[8], 0));
         std::vector<infft_plan_t> P;
         std::vector<const void*> F;
         std::vector<void*> H;
         std::vector<int> S;
-        for (int i : grp[g]) { P.push_back(plans[i]); F.push_back(f[i]); H.push_back(fhat[i]); S.push_back(slot[i]); }
+        for (int i : grp[g]) { P.push_back(plans[i]); F.push_back(fin[i]); H.push_back(fhat[i]); S.push_back(slot[i]); }
         if (!P.empty() && s == INFFT_OK)
             s = run_batched(P.data(), (int)P.size(), mode, F.data(), H.data(), b->s[g], nullptr, S.data(), false);
         INFFT_CUDA(cudaEventRecord(b->e[g], b->s[g]));
@@ -1005,12 +1036,17 @@ infft_status infft_batch_create(const infft_plan_t* plans, int count, int mode, 
     // the jobs in concurrent branches of unequal work, as in run_branched
     const int G = branch_count(plans, count, host);
     const std::vector<std::vector<int>> grp = split_groups(plans, count, G);
-    cudaStream_t cap;
+    bool host_in = false;
+    for (int i = 0; i < count; ++i) host_in = host_in || !is_device_pointer(f[i]);
+    cudaStream_t cap, cs;
     INFFT_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    INFFT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     std::vector<cudaStream_t> br(G, nullptr);
     std::vector<cudaEvent_t> ev(G + 1, nullptr);       // branch ends, fork
+    std::vector<cudaEvent_t> rd(G + 1, nullptr);       // inputs of a branch arrived; all copies issued
     for (int g = 0; g < G; ++g) INFFT_CUDA(cudaStreamCreateWithFlags(&br[g], cudaStreamNonBlocking));
     for (int g = 0; g <= G; ++g) INFFT_CUDA(cudaEventCreateWithFlags(&ev[g], cudaEventDisableTiming));
+    for (int g = 0; g <= G; ++g) INFFT_CUDA(cudaEventCreateWithFlags(&rd[g], cudaEventDisableTiming));
     infft_batch_s* b = new infft_batch_s();
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     infft_status s = INFFT_OK;
@@ -1019,13 +1055,15 @@ infft_status infft_batch_create(const infft_plan_t* plans, int count, int mode, 
         s = INFFT_ECUDA;
     } else {
         cudaEventRecord(ev[G], cap);
+        for (int g = 0; g < G; ++g) cudaStreamWaitEvent(br[g], ev[G], 0);
+        std::vector<const void*> fin(f, f + count);
+        if (host_in) s = stage_inputs(plans, grp, f, fin, cap, cs, ev[G], rd.data(), rd[G], br.data());
         for (int g = 0; g < G && s == INFFT_OK; ++g) {
-            cudaStreamWaitEvent(br[g], ev[G], 0);
             std::vector<infft_plan_t> P;
             std::vector<const void*> F;
             std::vector<void*> H;
             std::vector<int> S;
-            for (int i : grp[g]) { P.push_back(plans[i]); F.push_back(f[i]); H.push_back(fhat[i]); S.push_back(slot[i]); }
+            for (int i : grp[g]) { P.push_back(plans[i]); F.push_back(fin[i]); H.push_back(fhat[i]); S.push_back(slot[i]); }
             if (!P.empty())
                 s = run_batched(P.data(), (int)P.size(), mode, F.data(), H.data(), br[g], nullptr, S.data(), false);
             cudaEventRecord(ev[g], br[g]);
@@ -1034,8 +1072,10 @@ infft_status infft_batch_create(const infft_plan_t* plans, int count, int mode, 
         e = cudaStreamEndCapture(cap, &b->graph);
     }
     cudaStreamDestroy(cap);
+    cudaStreamDestroy(cs);
     for (int g = 0; g < G; ++g) cudaStreamDestroy(br[g]);
     for (int g = 0; g <= G; ++g) cudaEventDestroy(ev[g]);
+    for (int g = 0; g <= G; ++g) cudaEventDestroy(rd[g]);
     if (s != INFFT_OK || e != cudaSuccess) {
         if (s == INFFT_OK) set_error("end capture: %s", cudaGetErrorString(e));
         if (b->graph) cudaGraphDestroy(b->graph);

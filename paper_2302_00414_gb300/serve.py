@@ -61,8 +61,10 @@ class Backend:
     """GPU backend over the library: plans, batched launches, completion events."""
 
     def __init__(self, weights_iters: int = 30, m: int = 4, sigma: float = 2.0, bopt: bool = False):
-        """bopt: also optimise B (Algorithm 4.3) when a point set is admitted, and serve
-        its reconstructions with B_opt (Algorithm 4.4) instead of the weights (Algorithm 3.7)."""
+        """bopt: also optimise B (Algorithm 4.3) when a two-dimensional point set is admitted,
+        and serve its reconstructions with B_opt (Algorithm 4.4) instead of the weights
+        (Algorithm 3.7).  Three-dimensional sets keep the weights: with (2m+2)^3 = 1000 slots
+        per point and M_sigma^3 columns their B_opt takes minutes per set on one GPU."""
         import torch
 
         import paper_2302_00414_gb300 as L
@@ -84,7 +86,7 @@ class Backend:
         t2 = time.perf_counter()
         p.weights(max_iter=self.weights_iters, rel_tol=1e-12, stream=stream.cuda_stream)
         t3 = time.perf_counter()
-        if self.bopt:
+        if self.bopt and ps.d == 2:
             p.optimize_B(stream=stream.cuda_stream)
         t4 = time.perf_counter()
         self.phase_s["points"] += t1 - t0
@@ -101,7 +103,7 @@ class Backend:
         grid = (2 * ps.M) ** ps.d
         cg = 16 * ((4 * ps.M) ** ps.d) * 8   # float64 grids and scratch of the degree-2M solve
         extra = 0
-        if self.bopt:   # float64 and plan-precision coefficients, the solve's member lists and V
+        if self.bopt and ps.d == 2:   # float64 and plan-precision coefficients, member lists and V
             extra = n * (2 * self.m + 2) ** ps.d * (16 + 8 + 8) + 16 * n * ps.d * (2 * self.m + 2)
         return 120 * n + 40 * grid + cg + extra
 
@@ -128,7 +130,8 @@ class Backend:
             for f in fs:
                 f.record_stream(stream)
             t1 = time.perf_counter()
-            self.L.adjoint_batched(plans, fs, outs, self.mode, stream=stream.cuda_stream, slots=slots)
+            mode = self.mode if plans[0].d == 2 else self.L.MODE_DCF   # a batch has one d
+            self.L.adjoint_batched(plans, fs, outs, mode, stream=stream.cuda_stream, slots=slots)
             t2 = time.perf_counter()
             ev = torch.cuda.Event()
             ev.record(stream)

@@ -62,3 +62,20 @@ def test_reference_arm_works_on_rank_0_only(capsys):
         sys.argv = argv
     assert bench.run_reference(args, rank=1, world=2) is None
     assert capsys.readouterr().out == ""
+
+
+def test_oracle_sample_keeps_the_batch_mix():
+    """The reference arm and the CPU baseline time complete sets, four of every degree M per
+    step, taken in turn, so the sample keeps the batch's even mix of M and every set is
+    reached."""
+    import bench
+    import inputs
+    sets = inputs.batch_sets(64, 0)
+    seen = set()
+    for step in range(8):
+        pick = bench.oracle_sample(sets, step, 4)
+        Ms = [sets[i][0] for i in pick]
+        assert sorted(set(Ms)) == sorted({M for M, _ in sets})
+        assert all(Ms.count(M) == 4 for M in set(Ms))
+        seen.update(pick)
+    assert seen == set(range(len(sets)))

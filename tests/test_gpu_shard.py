@@ -51,3 +51,27 @@ def test_step_calls_reject_bad_arguments():
     h = np.zeros(32 * 32, dtype=np.complex64)
     f = torch.zeros(500, dtype=torch.complex64, device="cuda")
     assert api.infft_spread_grid(p.handle, L.MODE_PLAIN, f.data_ptr(), h.ctypes.data, 0) == L.EINVAL
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_fft_axis_matches_cufft(prec):
+    """infft_fft_axis (the pruned DFT along one axis with the deconvolution of eq. matrix_D)
+    against cuFFT (torch.fft) followed by the crop to I_M and the factors 1/(M_sigma w^(k)) of
+    the oracle's window transform: the library's FFT cross-checked by another FFT."""
+    L, torch = lib_or_skip()
+    from oracle import windows as W
+    from paper_2302_00414_gb300 import api
+    M, m = 64, 4
+    p = L.Plan(inputs.random_points(1000, 2, 4), M, 2.0, m, prec)
+    Ms = p.Ms
+    cd = torch.complex64 if prec == "fp32" else torch.complex128
+    k = np.arange(-M // 2, M // 2)
+    dinv = 1.0 / (Ms * W.what1(W.KB, k, M, Ms, m))
+    g = torch.randn(3, Ms, 5, dtype=cd, device="cuda")
+    for nblk in (1, 4):
+        out = torch.empty(3 * M * 5, dtype=cd, device="cuda")
+        s = api.infft_fft_axis(p.handle, L.MODE_PLAIN, 3, 5, nblk, g.data_ptr(), out.data_ptr(), 0)
+        assert s == L.OK, L.last_error()
+        ref = torch.fft.fft(g.to(torch.complex128), dim=1).cpu().numpy()[:, np.mod(k, Ms), :] * dinv[None, :, None]
+        got = out.cpu().numpy().reshape(nblk, 3, M // nblk, 5).transpose(1, 0, 2, 3).reshape(3, M, 5)
+        assert rel(got, ref) < (1e-6 if prec == "fp32" else 1e-13)
