@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--rate", type=float, default=500.0, help="C5: mean arrival rate (requests/s)")
     ap.add_argument("--requests", type=int, default=20000, help="C5: number of requests")
     ap.add_argument("--new-frac", type=float, default=0.2, help="C5: fraction of requests on new point sets")
+    ap.add_argument("--builders", type=int, default=3, help="C5: threads building new point sets")
     ap.add_argument("--bopt-on-admit", action="store_true",
                     help="C5: also optimise B (Algorithm 4.3) on admit and serve with B_opt (Algorithm 4.4)")
     ap.add_argument("--time-limit", type=float, default=120.0, help="C5: wall-clock cap of the serving run (s)")
@@ -486,8 +487,17 @@ def run_ours(args, rank, world, dist):
     # ---- end to end through the C ABI with pinned host buffers ---------------------------
     # (the graph of one step over page-locked host buffers: every replay copies the step's
     # samples in and its coefficients out; and the same through the per-call API)
-    f_host = [f.cpu().pin_memory() for f in fs]
-    h_host = [torch.empty(h.shape, dtype=h.dtype).pin_memory() for h in hs]
+    # the step's samples in one page-locked allocation (each set's vector a slice of it), and
+    # the results likewise, as a caller batching its requests would hold them
+    nf = [int(f.numel()) for f in fs]
+    nh = [int(h.numel()) for h in hs]
+    f_all = torch.empty(sum(nf), dtype=torch.complex64).pin_memory()
+    h_all = torch.empty(sum(nh), dtype=torch.complex64).pin_memory()
+    of, oh = np.cumsum([0] + nf), np.cumsum([0] + nh)
+    f_host = [f_all[of[i]:of[i + 1]] for i in range(len(fs))]
+    h_host = [h_all[oh[i]:oh[i + 1]].view(hs[i].shape) for i in range(len(hs))]
+    for a, f in zip(f_host, fs):
+        a.copy_(f.cpu())
     fh_np = [t.numpy() for t in f_host]
     hh_np = [t.numpy() for t in h_host]
     hbatch = L.Batch(plans, fh_np, hh_np, L.MODE_DCF)
@@ -817,7 +827,7 @@ def run_serving(args, rank, world, dist):
             return True
         return False
 
-    server = Server(be, mem_budget=budget, max_batch=32, streams=3, keep_output=keep)
+    server = Server(be, mem_budget=budget, max_batch=32, streams=3, keep_output=keep, builders=args.builders)
     meta = {}
     # one sample buffer per class, long enough for its largest N; a request on a set
     # with N points reads the first N entries

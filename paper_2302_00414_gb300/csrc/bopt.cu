@@ -373,9 +373,12 @@ static infft_status optimize_impl(infft_plan_s* p, unsigned opts, double* max_re
     g.real_field = (opts & INFFT_BOPT_REAL) ? 1 : 0;
     const long long ncols = ipow(g.Ms, g.d);
     const long long nent = (long long)g.N * g.NS;
+    // temporaries from the library's stream-ordered pool: unlike cudaMalloc / cudaFree they do
+    // not synchronise the device, so a server's reconstructions on other streams go on while a
+    // new point set's B_opt is computed
     auto alloc = [&](size_t bytes) -> void* {
         void* q = nullptr;
-        if (cudaMalloc(&q, std::max<size_t>(bytes, 16)) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+        if (pool_alloc(&q, std::max<size_t>(bytes, 16), st) != INFFT_OK) return nullptr;
         tmp.push_back(q);
         return q;
     };
@@ -443,10 +446,11 @@ static infft_status optimize_impl(infft_plan_s* p, unsigned opts, double* max_re
         else { big.push_back((int)c); n_big = std::max(n_big, n); }
     }
     std::stable_sort(big.begin(), big.end(), [&](int a, int b) { return hs[a + 1] - hs[a] > hs[b + 1] - hs[b]; });
-    // The solve goes out in short launches (about two columns per block each), so that the
-    // blocks leave the SMs every few milliseconds and work of higher-priority streams (a
+    // The solve goes out in launches of about sixteen columns per block (tens of milliseconds
+    // each), so that the blocks leave the SMs regularly and work of higher-priority streams (a
     // server's reconstructions while a new point set is admitted) is scheduled in between;
-    // each launch has its own work counter.
+    // each launch has its own work counter.  (Two columns per block made the tails of the
+    // launches cost half again the solve's time.)
     int* list = (int*)alloc((small.size() + big.size()) * 4);
     if (!list) { set_error("optimize_B: out of device memory (column lists)"); return INFFT_ENOMEM; }
     if (!small.empty())
@@ -459,7 +463,7 @@ static infft_status optimize_impl(infft_plan_s* p, unsigned opts, double* max_re
         INFFT_CUDA(cudaFuncSetAttribute(k_bopt_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         INFFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bopt_solve, BOPT_THREADS, smem));
         const int blocks = nsm * std::max(1, per_sm);
-        const long long chunk = 2LL * blocks;
+        const long long chunk = 16LL * blocks;
         const long long nchunk = ((long long)small.size() + chunk - 1) / chunk;
         int* next = (int*)alloc((size_t)nchunk * 4);   // one work counter per launch
         if (!next) { set_error("optimize_B: out of device memory (work counters)"); return INFFT_ENOMEM; }
@@ -540,8 +544,8 @@ infft_status infft_optimize_B(infft_plan_t p, unsigned opts, double* max_col_res
     std::vector<void*> tmp;
     p->pool_stream = (cudaStream_t)stream;
     infft_status s = optimize_impl(p, opts, max_col_residual, (cudaStream_t)stream, tmp);
+    for (void* q : tmp) pool_free(q, (cudaStream_t)stream);   // in stream order, after the solve
     cudaStreamSynchronize((cudaStream_t)stream);
-    for (void* q : tmp) cudaFree(q);
     return s;
 }
 

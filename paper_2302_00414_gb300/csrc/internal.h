@@ -75,6 +75,8 @@ struct infft_batch_s {
     cudaGraphExec_t exec = nullptr;
     void* jobs_dev = nullptr;
     int* prefix_dev = nullptr;
+    void* stage_in = nullptr;    // device staging of host inputs / outputs (host-buffer batches)
+    void* stage_out = nullptr;
 };
 
 namespace infft {

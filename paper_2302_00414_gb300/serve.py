@@ -151,7 +151,10 @@ class Backend:
 class Server:
     def __init__(self, backend, mem_budget: Optional[int] = None, max_batch: int = 64, streams: int = 3,
                  max_repeat: int = 8, clock: Callable[[], float] = time.perf_counter,
-                 keep_output: Optional[Callable[[Request], bool]] = None):
+                 keep_output: Optional[Callable[[Request], bool]] = None, builders: int = 1):
+        """builders: threads that build new point sets (plan, weights, B_opt), each on its own
+        low-priority stream, so that the latency-bound precompute kernels of several sets
+        overlap on the device."""
         self.be = backend
         # which completed requests keep their result tensor (all by default); dropping the
         # others lets the allocator reuse their memory instead of growing the heap
@@ -185,10 +188,13 @@ class Server:
         self._lock = threading.Lock()
         self._work: queue.Queue = queue.Queue()
         self._ready: queue.Queue = queue.Queue()
-        self._pstream = backend.new_stream(priority=0)
         self._slots_busy: Dict[Any, set] = collections.defaultdict(set)   # scratch sets in flight
-        self._worker = threading.Thread(target=self._precompute_loop, daemon=True)
-        self._worker.start()
+        self._workers = []
+        self._pstreams = [backend.new_stream(priority=0) for _ in range(max(1, builders))]
+        for st in self._pstreams:
+            t = threading.Thread(target=self._precompute_loop, args=(st,), daemon=True)
+            t.start()
+            self._workers.append(t)
         # evicted plans are destroyed off the scheduling thread: destroying a plan waits for
         # the device, which would stall every reconstruction behind the precompute's kernels
         self._released: queue.Queue = queue.Queue()
@@ -201,14 +207,14 @@ class Server:
         if pin:
             self.pinned.add(ps.key)
 
-    def _precompute_loop(self):
+    def _precompute_loop(self, stream):
         while True:
             ps = self._work.get()
             if ps is None:
                 return
             try:
                 t0 = time.perf_counter()
-                plan = self.be.build_plan(ps, self._pstream)
+                plan = self.be.build_plan(ps, stream)
                 self.build_times.append((ps.key, time.perf_counter() - t0))
                 self._ready.put((ps.key, plan, None))
             except Exception as e:  # surfaced to the requests of this key
@@ -386,8 +392,10 @@ class Server:
             time.sleep(0)
 
     def close(self):
-        self._work.put(None)
-        self._worker.join(timeout=5)
+        for _ in self._workers:
+            self._work.put(None)
+        for t in self._workers:
+            t.join(timeout=5)
         self._released.put(None)
         self._releaser.join(timeout=5)
 
@@ -398,8 +406,10 @@ class Server:
                 self._work.get_nowait()
             except queue.Empty:
                 break
-        self._work.put(None)
-        self._worker.join(timeout=timeout)
+        for _ in self._workers:
+            self._work.put(None)
+        for t in self._workers:
+            t.join(timeout=timeout)
         self._released.put(None)
         self._releaser.join(timeout=timeout)
 

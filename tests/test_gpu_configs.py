@@ -103,6 +103,24 @@ def test_graph_batch_over_pinned_host_buffers():
         torch.cuda.synchronize()
         for a, b in zip(hh, hd):
             assert np.array_equal(a.numpy(), b.cpu().numpy())
+    # the samples and results as slices of one page-locked allocation each: the graph copies
+    # adjacent ranges at once; same results
+    nf = [int(t.numel()) for t in fh]
+    nh = [M * M for M, _ in sets]
+    fa = torch.empty(sum(nf), dtype=torch.complex64).pin_memory()
+    ha = torch.zeros(sum(nh), dtype=torch.complex64).pin_memory()
+    of, oh = np.cumsum([0] + nf), np.cumsum([0] + nh)
+    fs2 = [fa[of[i]:of[i + 1]] for i in range(len(sets))]
+    for a, t in zip(fs2, fh):
+        a.copy_(t)
+    hs2 = [ha[oh[i]:oh[i + 1]].view(M, M) for i, (M, _) in enumerate(sets)]
+    hb2 = L.Batch(plans, [t.numpy() for t in fs2], [t.numpy() for t in hs2], L.MODE_DCF)
+    for rep in range(2):
+        ha.zero_()
+        hb2.run()
+        torch.cuda.synchronize()
+        for a, b in zip(hs2, hd):
+            assert np.array_equal(a.numpy(), b.cpu().numpy())
     pageable = [np.zeros((M, M), dtype=np.complex64) for M, _ in sets]
     with pytest.raises(L.InfftError):
         L.Batch(plans, [t.numpy() for t in fh], pageable, L.MODE_DCF)

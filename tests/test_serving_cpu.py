@@ -183,8 +183,24 @@ def test_pinned_point_sets_are_never_evicted():
 
 
 def test_reconstruction_streams_outrank_the_precompute_stream():
-    s = Server(FakeBackend(), streams=3)
-    assert all(st[1] < s._pstream[1] for st in s.streams)
+    s = Server(FakeBackend(), streams=3, builders=2)
+    assert len(s._pstreams) == 2
+    assert all(st[1] < ps[1] for st in s.streams for ps in s._pstreams)
+    s.close()
+
+
+def test_several_builders_build_every_set_once():
+    """With three build threads every registered set is built exactly once and every request
+    completes, whatever order the builds finish in."""
+    be = FakeBackend(latency=1)
+    s = Server(be, streams=2, builders=3)
+    for k in range(9):
+        s.register(PointSet(key=k, d=2, M=8, x=None, N=10))
+    for i in range(27):
+        s.submit(Request(rid=i, key=i % 9, f=i))
+    s.drain(timeout=30)
+    assert len(s.completed) == 27
+    assert sorted(k for k, _ in s.build_times) == list(range(9))
     s.close()
 
 
