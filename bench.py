@@ -441,9 +441,15 @@ def run_ours(args, rank, world, dist):
     Kc = coeffs
     Mrow = sum(p.Ms * M for p, (M, _) in zip(plans, sets))
     stage_roof = {}
-    for name, nbytes, ms in (("merge", padded + 8 * G, merge_ms),
-                             ("fft_pass1", 8 * G + 8 * Mrow, fft_ms[0]),
-                             ("fft_pass2", 8 * Mrow + 8 * Kc, fft_ms[1])):
+    if merge_ms < 4e-3:   # back-to-back events around no kernel
+        # the first pass merges the padded tiles as it loads its rows: no grid in between
+        stages = (("merge+fft_pass1", padded + 8 * Mrow, fft_ms[0]),
+                  ("fft_pass2", 8 * Mrow + 8 * Kc, fft_ms[1]))
+    else:
+        stages = (("merge", padded + 8 * G, merge_ms),
+                  ("fft_pass1", 8 * G + 8 * Mrow, fft_ms[0]),
+                  ("fft_pass2", 8 * Mrow + 8 * Kc, fft_ms[1]))
+    for name, nbytes, ms in stages:
         if ms > 0:
             gbs = nbytes / (ms / 1e3) / 1e9
             stage_roof[name] = {"bytes": int(nbytes), "ms": ms, "achieved": gbs, "frac": gbs / peak}

@@ -237,7 +237,10 @@ infft_status infft_get_bopt(infft_plan_t plan, void* coeff, void* stream);
  * memory while they spread the current ones (d = 3: always; d = 2: float32 with m <= 4,
  * and grids with fewer work items than eight warps per SM).  INFFT_SPREAD2D_PREFETCH and
  * INFFT_SPREAD3D_PREFETCH in the environment ("0" off, "1" on) override that choice; the
- * sums and their order, and so the results bit for bit, are the same either way.
+ * sums and their order, and so the results bit for bit, are the same either way.  So with
+ * INFFT_FFT_MERGE (on unless "0"): for d = 2 the first FFT pass sums each grid cell from the
+ * padded tiles as it loads its rows (steps 2-3 of Algorithm 2.4 with no grid written in
+ * between) instead of a separate halo-merge kernel.
  */
 infft_status infft_adjoint(infft_plan_t plan, int mode, const void* f, void* fhat, void* stream);
 
@@ -319,7 +322,9 @@ infft_status infft_adjoint_batched_slots(const infft_plan_t* plans, int count, i
  * reports device times of the stages in stage_ms[5]: spreading, halo merge and
  * the FFT passes along each axis (unused entries 0), from CUDA events recorded on
  * `stream` between the kernel launches.  Jobs whose plans turn on the fused merge-FFT
- * kernel (infft_tune_t fused_fft) count it in the merge stage.  Synchronises.
+ * kernel (infft_tune_t fused_fft) count it in the merge stage; where the first FFT pass does
+ * the merge as it loads (INFFT_FFT_MERGE, d = 2), the merge stage is 0 and the first pass
+ * holds it.  Synchronises.
  */
 infft_status infft_adjoint_batched_timed(const infft_plan_t* plans, int count, int mode,
                                          const void* const* f, void* const* fhat, void* stream,

@@ -293,6 +293,16 @@ __device__ __forceinline__ cx<R> merged_cell(const Job<R>& J, long long cidx) {
 // so that the bit-reversed scatter and the short butterfly strides spread over banks.
 __device__ __forceinline__ int skew(int i) { return i + (i >> 4); }
 
+// e / M for 0 <= e < 2^22 through a float32 reciprocal rM ~ 1/M and one correction step (the
+// estimate is off by at most one there): a few instructions instead of an integer division
+__device__ __forceinline__ int div_small(int e, int M, float rM) {
+    int q = __float2int_rz((float)e * rM);
+    const int r = e - q * M;
+    if (r < 0) --q;
+    else if (r >= M) ++q;
+    return q;
+}
+
 // lines of length n per FFT block: a 16 KB budget of complex elements, at most 32 lines (more,
 // smaller blocks hide the passes' load latency better: batched d = 2, n = 512: 64 / 32 / 16 / 8 KB
 // of lines per block gave FFT passes of 0.140 / 0.109 / 0.100 / 0.104 ms).  Per job, so that the
@@ -303,7 +313,15 @@ __host__ __device__ inline int fft_lines(int n, int elem) {
     return L;
 }
 
-template <class R, int D, bool FWD>
+// rows of tiles whose item ranges a merge-on-load block of L lines (grid rows) consults: its
+// own one or L / T, and one above and below
+__host__ __device__ inline int mrg_tile_rows(int L, int T) { return (L <= T ? 1 : L / T) + 2; }
+
+// With MRG (d = 2 adjoint, pass 0 only) the block's lines are grid rows whose cells are summed
+// from the padded tiles as they are loaded: the halo merge of k_merge2d in the same order per
+// cell, with no grid written or read in between.  The item ranges of the tiles the block's
+// rows draw on are staged in shared memory after the twiddles first.
+template <class R, int D, bool FWD, bool MRG = false>
 __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> js, int pass) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<R>* buf = reinterpret_cast<cx<R>*>(smem_raw);
@@ -358,7 +376,64 @@ __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> j
     }
     __syncthreads();
 
-    if (!FWD) {
+    if (MRG && pass == 0) {
+        const int T = J.T, m = J.m, P = J.P, nt = J.ntile;
+        const int logT = 31 - __clz(T), lognt = 31 - __clz(nt);
+        const int ty0 = (int)(q0 >> logT);
+        const int ntr = mrg_tile_rows(L, T);
+        int2* rng = reinterpret_cast<int2*>(tws + (n >> 1));   // [ntr][nt] first item, count
+        for (int k = tid; k < ntr * nt; k += nth) {
+            const int tyw = (ty0 - 1 + (k >> lognt)) & (nt - 1), tx = k & (nt - 1);
+            const int a = __ldg(J.tile_items + tyw * nt + tx), b = __ldg(J.tile_items + tyw * nt + tx + 1);
+            rng[k] = make_int2(a, b - a);
+        }
+        __syncthreads();
+        const size_t cells = (size_t)P * P;
+#pragma unroll 2
+        for (int e = tid; e < L * n; e += nth) {
+            int l, i;
+            if (lanes_b) { l = e & (L - 1); i = e >> logL; } else { i = e & (n - 1); l = e >> logn; }
+            const long long y = q0 + l;
+            cx<R> acc = mk<R>(0, 0);
+            if (y < nlines) {
+                const int r = (int)y & (T - 1), ty = (int)(y >> logT), c = i & (T - 1), tx = i >> logT;
+                int yd[2], yo[2], xd[2], xo[2], ny = 1, nx = 1;
+                yd[0] = 0; yo[0] = r + m;
+                xd[0] = 0; xo[0] = c + m;
+                if (r + T + m < P) { yd[1] = -1; yo[1] = r + T + m; ny = 2; }
+                else if (r - T + m >= 0) { yd[1] = 1; yo[1] = r - T + m; ny = 2; }
+                if (c + T + m < P) { xd[1] = -1; xo[1] = c + T + m; nx = 2; }
+                else if (c - T + m >= 0) { xd[1] = 1; xo[1] = c - T + m; nx = 2; }
+                // the first item of every source, loaded together; then the sum in source order
+                size_t src0[4];
+                int cnt[4];
+                cx<R> v[4];
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) {
+                        const int q = 2 * a + b;
+                        cnt[q] = 0;
+                        src0[q] = 0;
+                        if (a < ny && b < nx) {
+                            const int2 g = rng[((ty + yd[a] - ty0 + 1) << lognt) + ((tx + xd[b]) & (nt - 1))];
+                            cnt[q] = g.y;
+                            src0[q] = (size_t)g.x * cells + (size_t)yo[a] * P + xo[b];
+                        }
+                    }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] = cnt[q] > 0 ? J.padded[src0[q]] : mk<R>(0, 0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (cnt[q] <= 0) continue;
+                    acc = add(acc, v[q]);
+#pragma unroll 1
+                    for (int k = 1; k < cnt[q]; ++k) acc = add(acc, J.padded[src0[q] + (size_t)k * cells]);
+                }
+            }
+            buf[l * ns + skew(bitrev(i, logn))] = acc;
+        }
+    } else if (!FWD) {
         // each thread issues the loads of up to eight elements before storing any, so that
         // the block waits for one global-load latency rather than eight in a row
         constexpr int KL = 8;
@@ -386,13 +461,14 @@ __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> j
     } else {
         for (int e = tid; e < L * ns; e += nth) buf[e] = mk<R>(0, 0);
         __syncthreads();
+        const float rM = 1.f / (float)M;
         for (int e = tid; e < L * M; e += nth) {
             int l, i;
-            if (lanes_b) { l = e & (L - 1); i = e >> logL; } else { i = e % M; l = e / M; }
+            if (lanes_b) { l = e & (L - 1); i = e >> logL; } else { l = div_small(e, M, rM); i = e - l * M; }
             const long long g0 = s_in[l];
             if (g0 >= 0) {
                 const cx<R> v = scale(src[g0 + (long long)i * B], J.dinv[i]);
-                const int bin = mod_pos(i - M / 2, Ms);
+                const int bin = (i - M / 2) & (n - 1);   // n = M_sigma is a power of two
                 buf[l * ns + skew(bitrev(bin, logn))] = v;
             }
         }
@@ -449,16 +525,30 @@ __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> j
     }
 
     if (!FWD) {
-        for (int e = tid; e < L * M; e += nth) {
-            int l, i;
-            if (lanes_b) { l = e & (L - 1); i = e >> logL; } else { i = e % M; l = e / M; }
-            const long long g0 = s_out[l];
-            if (g0 >= 0) {
-                const int bin = mod_pos(i - M / 2, Ms);
-                // block i / MB of the middle index holds the (A, MB, B) tensor of its indices
-                const long long o = (long long)(i / MB) * A * MB * B + (long long)(i % MB) * B;
-                dst[g0 + o] = scale(buf[l * ns + skew(bin)], J.dinv[i]);
+        if (expl) {
+            for (int e = tid; e < L * M; e += nth) {
+                int l, i;
+                if (lanes_b) { l = e & (L - 1); i = e >> logL; } else { i = e % M; l = e / M; }
+                const long long g0 = s_out[l];
+                if (g0 >= 0) {
+                    const int bin = (i - M / 2) & (n - 1);
+                    // block i / MB of the middle index holds the (A, MB, B) tensor of its indices
+                    const long long o = (long long)(i / MB) * A * MB * B + (long long)(i % MB) * B;
+                    dst[g0 + o] = scale(buf[l * ns + skew(bin)], J.dinv[i]);
+                }
             }
+        } else if (lanes_b) {
+            for (int e = tid; e < L * M; e += nth) {
+                const int l = e & (L - 1), i = e >> logL;
+                const long long g0 = s_out[l];
+                if (g0 >= 0) dst[g0 + (long long)i * B] = scale(buf[l * ns + skew((i - M / 2) & (n - 1))], J.dinv[i]);
+            }
+        } else {   // nth / L threads per line (both powers of two), no division per element
+            const int tpl = nth >> logL, l = tid / tpl;
+            const long long g0 = s_out[l];
+            if (g0 >= 0)
+                for (int i = tid & (tpl - 1); i < M; i += tpl)
+                    dst[g0 + (long long)i * B] = scale(buf[l * ns + skew((i - M / 2) & (n - 1))], J.dinv[i]);
         }
     } else {
         for (int e = tid; e < L * n; e += nth) {
@@ -636,6 +726,43 @@ static infft_status launch_fft_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent
     return INFFT_OK;
 }
 
+// The halo merge of the d = 2 register-row path folded into the first FFT pass (k_fft with
+// MRG), unless INFFT_FFT_MERGE=0 or a job's table of tile item ranges would pass 16 KB: the
+// grid is then neither written nor read between the two.  Both forms give bitwise the same
+// result.
+template <class R>
+static bool merge_on_load_ok(const JobSet<R>& js) {
+    if (env_form("INFFT_FFT_MERGE") == 0 || js.axA > 0) return false;
+    for (int j = 0; j < js.njobs; ++j) {
+        const Job<R>& J = js.job[j];
+        const int L = pick_lines(J.Ms, sizeof(cx<R>));
+        if ((size_t)mrg_tile_rows(L, J.T) * J.ntile * sizeof(int2) > 16 * 1024) return false;
+    }
+    return true;
+}
+
+template <class R>
+static infft_status launch_fft_adjoint_mrg(JobSet<R>& js, cudaStream_t st, cudaEvent_t* ev) {
+    size_t msmem = 0;
+    for (int j = 0; j < js.njobs; ++j) {
+        const Job<R>& J = js.job[j];
+        const int n = J.Ms, L = pick_lines(n, sizeof(cx<R>));
+        const size_t b = ((size_t)L * (n + n / 16) + n / 2) * sizeof(cx<R>) +
+                         (size_t)mrg_tile_rows(L, J.T) * J.ntile * sizeof(int2);
+        msmem = std::max(msmem, b);
+    }
+    INFFT_CUDA(cudaFuncSetAttribute(k_fft<R, 2, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem));
+    k_fft<R, 2, false, true><<<js.pre_fft[0][js.njobs], 256, msmem, st>>>(js, 0);
+    INFFT_LAUNCHED();
+    if (ev) INFFT_CUDA(cudaEventRecord(ev[3], st));
+    const size_t fsmem = fft_smem(js);
+    INFFT_CUDA(cudaFuncSetAttribute(k_fft<R, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
+    k_fft<R, 2, false><<<js.pre_fft[1][js.njobs], 256, fsmem, st>>>(js, 1);
+    INFFT_LAUNCHED();
+    if (ev) INFFT_CUDA(cudaEventRecord(ev[4], st));
+    return INFFT_OK;
+}
+
 template <class R, int D>
 static infft_status launch_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* ev, bool grid_only = false) {
     fill_prefixes(js, D, false);
@@ -660,6 +787,12 @@ static infft_status launch_adjoint(JobSet<R>& js, cudaStream_t st, cudaEvent_t* 
         JobSet<R>& jr = (int)rest.size() == js.njobs ? js : *new_subset(js, rest);
         std::unique_ptr<JobSet<R>> own(&jr == &js ? nullptr : &jr);
         if (own) fill_prefixes(jr, D, false);
+        if constexpr (D == 2) {
+            if (!grid_only && merge_on_load_ok(jr)) {
+                if (ev) INFFT_CUDA(cudaEventRecord(ev[2], st));   // the merge is timed with pass 0
+                return launch_fft_adjoint_mrg<R>(jr, st, ev);
+            }
+        }
         jr.pre_merge[0] = 0;
         for (int j = 0; j < jr.njobs; ++j) jr.pre_merge[j + 1] = jr.pre_merge[j] + jr.job[j].ntile * jr.job[j].ntile;
         k_merge2d<R><<<jr.pre_merge[jr.njobs], 256, 0, st>>>(jr);

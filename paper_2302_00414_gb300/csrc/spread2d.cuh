@@ -373,6 +373,10 @@ static bool spread2d_eligible(const JobSet<R>& js, int* m_out, bool* bopt_out) {
     for (int j = 0; j < js.njobs; ++j) {
         const Job<R>& J = js.job[j];
         if (J.d != 2 || J.m != m || (J.mode == INFFT_MODE_BOPT) != bopt || J.P > 32) return false;
+        // the two-source halo merge that follows needs P <= 2T, i.e. 2m <= T (2m + 1 <= T with
+        // B_opt's extra slot): a tuned tile of 8 at m >= 5 (m >= 4 with B_opt) puts some cells
+        // in three tiles along an axis, which the generic path handles
+        if (J.P > 2 * J.T) return false;
         if (!bopt && spread2d_pair_m<R>(m) && (J.P & 1)) return false;   // paired rows: 16-byte stores
     }
     if (m < 2 || m > 8) return false;   // m = 8 with window taps only: P = 16 + 16 <= 32

@@ -11,6 +11,7 @@ import pytest
 
 import inputs
 from oracle import fourier as FO
+from oracle import bopt as BO
 from oracle import nfft as NF
 from tests.gpu_util import lib_or_skip, rel, to_dev
 
@@ -250,6 +251,56 @@ def test_spread3d_prefetch_forms_equal(prec, gen, monkeypatch):
     assert rel(out["1"], ref) < (1e-5 if prec == "fp32" else 1e-12)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("mode", ["plain", "dcf", "bopt"])
+@pytest.mark.parametrize("M,tile", [(8, 0), (32, 0), (64, 0), (256, 0), (64, 8)])
+def test_merge_on_load_equals_merge_kernel(prec, mode, M, tile, monkeypatch):
+    """The first FFT pass summing the padded tiles as it loads (Algorithm 2.4 steps 2-3 without
+    the grid in between) gives bitwise the result of the halo-merge kernel followed by the
+    pass, alone and in a batch of grid sizes; both follow the oracle's Algorithm 2.4 / 4.4.
+    M = 8 has one tile (every neighbour wraps onto it), M = 64 with tiles of 8 blocks of 32
+    lines spanning four tile rows."""
+    L, torch = lib_or_skip()
+    if mode == "bopt" and M > 64:
+        pytest.skip("B_opt at this size is covered by the headline-size tests")
+    N = 3 * M * M
+    x = inputs.random_points(N, 2, 800 + M)
+    f = inputs.samples_complex(N, 801 + M)
+    w = inputs.rng(802 + M).uniform(0.5, 1.5, N) / N
+    cd = torch.complex64 if prec == "fp32" else torch.complex128
+    tune = {"tile": tile} if tile else None
+    p = L.Plan(x, M, 2.0, 4 if mode != "bopt" else 3, prec, tune=tune)
+    m = 4 if mode != "bopt" else 3
+    md = {"plain": L.MODE_PLAIN, "dcf": L.MODE_DCF, "bopt": L.MODE_BOPT}[mode]
+    if mode == "dcf":
+        p.set_weights(w.astype(np.complex128))
+    if mode == "bopt":
+        p.optimize_B()
+    fd = to_dev(torch, f, cd)
+    q = L.Plan(inputs.random_points(2000, 2, 803), 16, 2.0, m, prec, tune=tune)
+    if mode == "dcf":
+        q.set_weights(np.full(2000, 1 / 2000, dtype=np.complex128))
+    if mode == "bopt":
+        q.optimize_B()
+    g = to_dev(torch, inputs.samples_complex(2000, 804), cd)
+    out, bat = {}, {}
+    for form in ("0", "1"):
+        monkeypatch.setenv("INFFT_FFT_MERGE", form)
+        out[form] = p.adjoint(fd, mode=md).cpu().numpy().ravel()
+        h1 = torch.empty((16, 16), dtype=cd, device="cuda")
+        h2 = torch.empty((M, M), dtype=cd, device="cuda")
+        L.adjoint_batched([q, p], [g, fd], [h1, h2], md)
+        bat[form] = h2.cpu().numpy().ravel()
+    assert np.array_equal(out["0"], out["1"])
+    assert np.array_equal(bat["1"], out["1"])
+    assert np.array_equal(bat["0"], bat["1"])
+    if mode == "bopt":
+        ref = BO.reconstruct(x, f, p.get_bopt(), M, 2.0, m, "kb", BO.PATTERN_2M2)
+    else:
+        ref = NF.adjoint_nfft(x, f * w if mode == "dcf" else f, M, 2.0, m)
+    assert rel(out["1"], ref) < (1e-5 if prec == "fp32" else 1e-12)
+
+
 @pytest.mark.parametrize("m", [2, 3, 5])
 @pytest.mark.parametrize("gen", ["random", "clustered"])
 def test_fp32_d2_other_m_match_oracle_algorithm(m, gen):
@@ -364,6 +415,37 @@ def test_tuned_plans_give_the_same_reconstruction(tune):
         assert rel(outs["tuned"][i], outs["default"][i]) < 1e-6
         f = inputs.samples_complex(x.shape[0], 710 + i).astype(np.complex64).astype(np.complex128)
         assert rel(outs["tuned"][i], NF.adjoint_nfft(x, f / x.shape[0], M, 2.0, 4)) < 1e-5
+
+
+@pytest.mark.parametrize("prec,m", [("fp32", 5), ("fp32", 7), ("fp64", 6)])
+def test_small_tile_wide_window_d2(prec, m):
+    """A tile of 8 with 2m > 8 puts some grid cells in three padded tiles along an axis; the
+    reconstruction still follows the oracle's Algorithm 2.4 (the two-source halo merge is not
+    used for it)."""
+    L, torch = lib_or_skip()
+    M = 32
+    x = points(2, 3001, "random", 61)
+    f = inputs.samples_complex(len(x), 62)
+    cdt = torch.complex64 if prec == "fp32" else torch.complex128
+    p = L.Plan(x, M, 2.0, m, prec, tune={"tile": 8})
+    h = p.adjoint(to_dev(torch, f, cdt)).cpu().numpy()
+    assert rel(h, NF.adjoint_nfft(x, f, M, 2.0, m)) < (1e-5 if prec == "fp32" else 1e-12)
+
+
+def test_small_tile_bopt_d2():
+    """B_opt's padded tiles hold one more slot per axis (2m + 2): with a tile of 8 at m = 4 some
+    cells lie in three tiles along an axis.  Algorithm 4.4 still matches the oracle's with the
+    same B_opt."""
+    L, torch = lib_or_skip()
+    M, m = 16, 4
+    x = points(2, 1500, "random", 63)
+    f = inputs.samples_complex(len(x), 64)
+    p = L.Plan(x, M, 2.0, m, "fp64", tune={"tile": 8})
+    p.optimize_B()
+    coef = p.get_bopt()
+    h = p.adjoint(to_dev(torch, f, torch.complex128), mode=L.MODE_BOPT).cpu().numpy().ravel()
+    ref = BO.reconstruct(x, f, coef, M, 2.0, m, "kb", BO.PATTERN_2M2)
+    assert rel(h, ref) < 1e-12
 
 
 def test_invalid_tuning_is_rejected():
