@@ -344,6 +344,10 @@ __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> j
 
     cx<R>* tws = buf + L * ns;      // the n/2 twiddles after the lines
     for (int k = threadIdx.x; k < (Ms >> 1); k += blockDim.x) tws[k] = J.tw[k];
+    // then (merging pass only) the table of tile item ranges, then the M deconvolution factors
+    const int nrng = (MRG && pass == 0) ? mrg_tile_rows(L, J.T) * J.ntile : 0;
+    R* dvs = reinterpret_cast<R*>(reinterpret_cast<int2*>(tws + (Ms >> 1)) + nrng);
+    for (int k = threadIdx.x; k < M; k += blockDim.x) dvs[k] = J.dinv[k];
 
     const cx<R>* src;
     cx<R>* dst;
@@ -367,7 +371,12 @@ __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> j
         const long long q = q0 + tid;
         long long bi = -1, bo = -1;
         if (q < nlines) {
-            const long long a = q / B, b = q - a * B;
+            // a 32-bit division where the counts allow (a 64-bit one is a long software routine
+            // that the whole block would wait for)
+            long long a;
+            if (nlines <= 0x7fffffffLL && B <= 0x7fffffffLL) a = (long long)((unsigned)q / (unsigned)B);
+            else a = q / B;
+            const long long b = q - a * B;
             bi = (a * (FWD ? M : n)) * B + b;
             bo = (a * (FWD ? n : MB)) * B + b;
         }
@@ -467,7 +476,7 @@ __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> j
             if (lanes_b) { l = e & (L - 1); i = e >> logL; } else { l = div_small(e, M, rM); i = e - l * M; }
             const long long g0 = s_in[l];
             if (g0 >= 0) {
-                const cx<R> v = scale(src[g0 + (long long)i * B], J.dinv[i]);
+                const cx<R> v = scale(src[g0 + (long long)i * B], dvs[i]);
                 const int bin = (i - M / 2) & (n - 1);   // n = M_sigma is a power of two
                 buf[l * ns + skew(bitrev(bin, logn))] = v;
             }
@@ -534,21 +543,21 @@ __global__ void __launch_bounds__(256) k_fft(const __grid_constant__ JobSet<R> j
                     const int bin = (i - M / 2) & (n - 1);
                     // block i / MB of the middle index holds the (A, MB, B) tensor of its indices
                     const long long o = (long long)(i / MB) * A * MB * B + (long long)(i % MB) * B;
-                    dst[g0 + o] = scale(buf[l * ns + skew(bin)], J.dinv[i]);
+                    dst[g0 + o] = scale(buf[l * ns + skew(bin)], dvs[i]);
                 }
             }
         } else if (lanes_b) {
             for (int e = tid; e < L * M; e += nth) {
                 const int l = e & (L - 1), i = e >> logL;
                 const long long g0 = s_out[l];
-                if (g0 >= 0) dst[g0 + (long long)i * B] = scale(buf[l * ns + skew((i - M / 2) & (n - 1))], J.dinv[i]);
+                if (g0 >= 0) dst[g0 + (long long)i * B] = scale(buf[l * ns + skew((i - M / 2) & (n - 1))], dvs[i]);
             }
         } else {   // nth / L threads per line (both powers of two), no division per element
             const int tpl = nth >> logL, l = tid / tpl;
             const long long g0 = s_out[l];
             if (g0 >= 0)
                 for (int i = tid & (tpl - 1); i < M; i += tpl)
-                    dst[g0 + (long long)i * B] = scale(buf[l * ns + skew((i - M / 2) & (n - 1))], J.dinv[i]);
+                    dst[g0 + (long long)i * B] = scale(buf[l * ns + skew((i - M / 2) & (n - 1))], dvs[i]);
         }
     } else {
         for (int e = tid; e < L * n; e += nth) {
@@ -658,7 +667,7 @@ static size_t fft_smem(const JobSet<R>& js) {
     size_t mx = 0;
     for (int j = 0; j < js.njobs; ++j) {
         const int n = js.job[j].Ms, L = pick_lines(n, sizeof(cx<R>));
-        mx = std::max(mx, ((size_t)L * (n + n / 16) + n / 2) * sizeof(cx<R>));
+        mx = std::max(mx, ((size_t)L * (n + n / 16) + n / 2) * sizeof(cx<R>) + (size_t)js.job[j].M * sizeof(R));
     }
     return mx;
 }
@@ -748,7 +757,7 @@ static infft_status launch_fft_adjoint_mrg(JobSet<R>& js, cudaStream_t st, cudaE
         const Job<R>& J = js.job[j];
         const int n = J.Ms, L = pick_lines(n, sizeof(cx<R>));
         const size_t b = ((size_t)L * (n + n / 16) + n / 2) * sizeof(cx<R>) +
-                         (size_t)mrg_tile_rows(L, J.T) * J.ntile * sizeof(int2);
+                         (size_t)mrg_tile_rows(L, J.T) * J.ntile * sizeof(int2) + (size_t)J.M * sizeof(R);
         msmem = std::max(msmem, b);
     }
     INFFT_CUDA(cudaFuncSetAttribute(k_fft<R, 2, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem));
