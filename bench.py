@@ -479,6 +479,33 @@ def run_ours(args, rank, world, dist):
     except Exception as e:   # the cross-check is optional
         cufft_ms = f"unavailable: {type(e).__name__}"
 
+    # ---- the persistent form (one launch per step over all 64 sets; off by default because
+    # the staged graph above is faster): a graph of it, replayed and event-timed the same way
+    persistent = None
+    try:
+        os.environ["INFFT_PERSISTENT"] = "1"
+        hp = [torch.empty_like(h) for h in hs]
+        pb = L.Batch(plans, fs, hp, L.MODE_DCF)
+        for _ in range(3):
+            pb.run()
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(args.steps):
+            pb.run()
+        p1.record(stream)
+        torch.cuda.synchronize()
+        pms = p0.elapsed_time(p1) / args.steps
+        same = all(torch.equal(a, b) for a, b in zip(hp, hs))
+        persistent = {"ms_per_step": pms, "recon_per_s": len(plans) / (pms / 1e3), "bitwise_equal_to_staged": same,
+                      "wait_timeouts": L.wait_timeouts(),
+                      "what": "one persistent kernel per step (spread, merging pass along x, pass along y as "
+                              "work units of one queue), graph-replayed; INFFT_PERSISTENT=1"}
+        pb.close()
+        del hp
+    finally:
+        os.environ.pop("INFFT_PERSISTENT", None)
+
     # ---- plain: one reconstruction at a time -----------------------------------------------
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -600,6 +627,7 @@ def run_ours(args, rank, world, dist):
                      "note": "achieved/peak/frac: HBM (algorithmic bytes / event-timed spread); the kernel is "
                              "bound on chip by the shared-memory pipe"},
         "stage_roofline": stage_roof,
+        "persistent": persistent,
         "cufft_crosscheck": {"ms": cufft_ms, "what": "torch.fft.fft2 (cuFFT) of the 64 oversampled grids, "
                              "unpruned, no deconvolution, one batched call per grid size; our two pruned "
                              "passes with deconvolution take stage_ms.fft"},

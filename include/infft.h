@@ -297,6 +297,19 @@ infft_status infft_inverse_adjoint(infft_plan_t plan, const void* h, void* f, vo
  * library forks from `stream` (at its priority) and joins back to it;
  * INFFT_BATCH_BRANCHES in the environment (1..8) changes the count.  Results do not depend
  * on the branching.
+ * Persistent form (no counterpart in the paper; on request, INFFT_PERSISTENT=1): a batch of at
+ * most 96 float32 d = 2 jobs in window modes (PLAIN or DCF) with m <= 4 and device buffers
+ * runs as one persistent kernel
+ * (after a small counter reset), whose CTAs take work units from a queue: the spread of four
+ * work items, a block of the FFT pass along x that merges the padded tiles, a block of the
+ * pass along y; a job's x blocks wait for its spread, its y blocks for its x blocks.  The jobs
+ * run largest first, and the queue interleaves the stages of consecutive jobs.  Each sum is
+ * formed in the same order as in the staged kernels, so the results are bitwise the same.
+ * It is slower than the staged kernels in graph branches on the batched workload measured
+ * (0.470 against 0.450 ms per 64-set step), hence off by default.  INFFT_PERSIST_LAG sets the
+ * distance, in waves of the kernel's CTAs, between a job's spread and its FFT blocks in the
+ * queue (default 4).  Tuned plans with fused_fft = 1 or prefetch = 2 take the staged kernels.
+ * infft_batch_create records the form in effect.
  */
 infft_status infft_adjoint_batched(const infft_plan_t* plans, int count, int mode,
                                    const void* const* f, void* const* fhat, void* stream);
@@ -379,6 +392,12 @@ int infft_plan_work_items(infft_plan_t plan);        /* work items (tile, point 
 size_t infft_plan_device_bytes(infft_plan_t plan);   /* device memory held by the plan */
 const char* infft_last_error(void);
 void infft_destroy(infft_plan_t plan);
+
+/* infft_wait_timeouts -- how many bounded waits of the persistent batched kernel (a unit
+ * waiting for the units it depends on) gave up after about a second since the library was
+ * loaded.  The queue order rules such waits out; a nonzero count means the results of the
+ * launches since the last check are not to be trusted.  Synchronous with the device. */
+unsigned int infft_wait_timeouts(void);
 
 /*
  * infft_inject_faults -- host-side fault injection for testing callers' error handling

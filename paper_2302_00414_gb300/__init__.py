@@ -8,7 +8,7 @@ from .api import (BOPT_PATTERN_2M2, BOPT_PATTERN_PAPER, BOPT_REAL, ECUDA, EINVAL
                   EUNSUPPORTED, EXPORTED, FP32, FP64, MODE_BOPT,
                   MODE_DCF, MODE_PLAIN, OK, WIN_BSPLINE, WIN_DIRICHLET, WIN_KB, Batch, InfftError, Plan,
                   adjoint_batched, adjoint_batched_timed, infft_adjoint, infft_adjoint_batched, infft_destroy, infft_forward,
-                  infft_optimize_B, infft_plan, infft_weights, last_error, launch_count, launch_count_reset, load,
+                  infft_optimize_B, infft_plan, infft_weights, last_error, launch_count, launch_count_reset, load, wait_timeouts,
                   WEIGHTS_AUTO, WEIGHTS_NFFT, WEIGHTS_TOEPLITZ, POOLED, inject_faults)
 
 __all__ = [n for n in dir() if not n.startswith("_")]

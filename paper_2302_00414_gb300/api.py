@@ -73,6 +73,7 @@ _SIGS = {
     "infft_last_error": (C.c_char_p, []),
     "infft_destroy": (None, [C.c_void_p]),
     "infft_launch_count": (C.c_uint64, []),
+    "infft_wait_timeouts": (C.c_uint, []),
     "infft_inject_faults": (None, [C.c_uint]),
     "infft_launch_count_reset": (None, []),
 }
@@ -107,6 +108,11 @@ def last_error() -> str:
 
 def launch_count() -> int:
     return int(load().infft_launch_count())
+
+
+def wait_timeouts() -> int:
+    """Bounded waits of the persistent batched kernel that gave up (infft_wait_timeouts)."""
+    return int(load().infft_wait_timeouts())
 
 
 def inject_faults(mask: int):
@@ -224,7 +230,7 @@ def _ptr(a):
 
 def _stream(stream):
     if stream is not None:
-        return int(stream)
+        return int(getattr(stream, "cuda_stream", stream))   # a torch stream or a handle
     try:
         import torch
         if torch.cuda.is_available():

@@ -178,4 +178,7 @@ infft_status run_fft_axis(const Job<R>& J, long long A, long long B, int nblk, c
 template <class R>
 infft_status run_fft_passes(const Job<R>& J, cudaStream_t st, bool forward);
 
+// bounded waits of the persistent d = 2 kernel that gave up since the library was loaded
+unsigned int persist_wait_timeouts();
+
 }  // namespace infft

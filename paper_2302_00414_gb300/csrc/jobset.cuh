@@ -18,7 +18,6 @@ struct JobSet {
     int wpb;                    // warps (items) per block of the spread / interpolation kernels
     int smem_per_warp;          // bytes of shared memory per warp (spread / interpolation)
     int L;                      // lines per block of the FFT passes
-    int fuse_merge;             // adjoint: first FFT pass gathers the padded tiles
     // one explicit adjoint FFT pass (axA > 0): J.grid as an (axA, Ms, axB) tensor -> J.out as
     // (axA, M, axB) in axblk blocks along the middle index (see run_fft_axis)
     long long axA, axB;

@@ -589,6 +589,7 @@ using namespace infft;
 extern "C" {
 
 const char* infft_last_error(void) { return g_err; }
+unsigned int infft_wait_timeouts(void) { return persist_wait_timeouts(); }
 uint64_t infft_launch_count(void) { return g_launches; }
 void infft_launch_count_reset(void) { g_launches = 0; }
 
@@ -870,6 +871,21 @@ static int branch_count(const infft_plan_t* plans, int count, bool host_buffers 
     return std::max(1, std::min(G, count));
 }
 
+// Batches that the persistent d = 2 kernel takes (on request, INFFT_PERSISTENT=1) run as a
+// whole in one branch: the kernel overlaps the jobs' stages itself (float32, window modes,
+// m <= 4, device buffers).  The kernel's launcher makes the final decision and otherwise falls
+// back to the staged kernels.
+static bool persistent_candidate(const infft_plan_t* plans, int count, int mode) {
+    if (mode == INFFT_MODE_BOPT || count > MAXJ) return false;
+    const char* e = getenv("INFFT_PERSISTENT");
+    if (!e || e[0] != '1') return false;
+    for (int i = 0; i < count; ++i) {
+        const infft_plan_s* p = plans[i];
+        if (p->d != 2 || p->fp64 || p->m > 4 || p->tune.fused_fft == 1) return false;
+    }
+    return true;
+}
+
 static std::vector<std::vector<int>> split_groups(const infft_plan_t* plans, int count, int G) {
     std::vector<std::vector<int>> grp(G);
     std::vector<int> order(count);
@@ -952,7 +968,17 @@ static infft_status run_branched(const infft_plan_t* plans, int count, int mode,
         host_out = host_out || !is_device_pointer(fhat[i]);
         host_in = host_in || !is_device_pointer(f[i]);
     }
-    const int G = branch_count(plans, count, host_in || host_out);
+    const bool one = !host_in && !host_out && persistent_candidate(plans, count, mode);
+    const int G = one ? 1 : branch_count(plans, count, host_in || host_out);
+    if (G == 1 && one) {   // the jobs largest first: the persistent queue's tail is then short
+        const std::vector<int> ord = split_groups(plans, count, 1)[0];
+        std::vector<infft_plan_t> P;
+        std::vector<const void*> F;
+        std::vector<void*> H;
+        std::vector<int> S;
+        for (int i : ord) { P.push_back(plans[i]); F.push_back(f[i]); H.push_back(fhat[i]); S.push_back(slot[i]); }
+        return run_batched(P.data(), count, mode, F.data(), H.data(), st, nullptr, S.data());
+    }
     if (G == 1) return run_batched(plans, count, mode, f, fhat, st, nullptr, slot.data());
     BranchSet* b = nullptr;
     INFFT_TRY(branch_set(st, &b));
@@ -1186,7 +1212,7 @@ infft_status infft_batch_create(const infft_plan_t* plans, int count, int mode, 
         host = host || hi || ho;
     }
     // the jobs in concurrent branches of unequal work, as in run_branched
-    const int G = branch_count(plans, count, host);
+    const int G = (!host && persistent_candidate(plans, count, mode)) ? 1 : branch_count(plans, count, host);
     if (host) return batch_create_host(plans, count, mode, f, fhat, slot, G, out);
     const std::vector<std::vector<int>> grp = split_groups(plans, count, G);
     bool host_in = false;

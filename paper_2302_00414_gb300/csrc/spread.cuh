@@ -37,6 +37,10 @@ infft_status spread2d_try(JobSet<R>& js, cudaStream_t st, bool* used);
 template <class R>
 infft_status spread3d_try(JobSet<R>& js, cudaStream_t st, bool* used);
 
+// The persistent batched d = 2 adjoint (spread, merging pass along x and pass along y as work
+// units of one launch) when every job qualifies; *used tells whether it ran.  Prefixes filled.
+infft_status persist2d_try(JobSet<float>& js, cudaStream_t st, bool* used);
+
 // Halo merge and both pruned FFT passes (with deconvolution) of d = 2 adjoint jobs as one
 // thread-block-cluster kernel per grid size, for the jobs whose grid it takes; `rest`
 // receives the indices of the jobs left to the two-kernel form.

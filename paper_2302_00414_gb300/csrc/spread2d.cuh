@@ -52,11 +52,10 @@ __host__ __device__ constexpr size_t spread2d_slot_bytes() {
 // data of the next 32 points (perm, cell, u, w) are copied to shared memory with cp.async
 // while the current ones are spread, so that staging waits only on the gather of the
 // samples f.
+// One warp spreads work item gitem (global over the JobSet's jobs); `base` is the warp's
+// shared memory.  The body of k_spread2d, and the spread units of the persistent d = 2 kernel.
 template <class R, int MM, bool BOPT, bool PF>
-// the paired form holds 2 (2m + 1) complex accumulators: at most 96 registers, so five 4-warp
-// blocks (20 warps) share an SM (the one-point form ran six at 80 registers)
-__global__ void __launch_bounds__(128, spread2d_pair<R, MM, BOPT>() ? 5 : 1)
-    k_spread2d(const __grid_constant__ JobSet<R> js) {
+__device__ __forceinline__ void spread2d_item(const JobSet<R>& js, const int gitem, unsigned char* base) {
     constexpr int W = 2 * MM + 1;              // window taps per axis
     constexpr int WE = spread2d_we<R, MM, BOPT>();   // stride of the staged rows
     constexpr int WR = BOPT ? W + 1 : W;       // rows held in registers
@@ -64,17 +63,13 @@ __global__ void __launch_bounds__(128, spread2d_pair<R, MM, BOPT>() ? 5 : 1)
     constexpr bool PAIR = spread2d_pair<R, MM, BOPT>();
     constexpr int PX = spread2d_pitch<R, MM, BOPT>();
     constexpr int NC = PAIR ? 2 : 1;           // columns per lane
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gitem = blockIdx.x * js.wpb + warp;
-    if (gitem >= js.pre_items[js.njobs]) return;
+    const int lane = threadIdx.x & 31;
     const int jb = find_job(js.pre_items, js.njobs, gitem);
     const Job<R>& J = js.job[jb];
     const int it = gitem - js.pre_items[jb];
     const int4 item = J.items[it];
     const int P = J.P, Ms = J.Ms, T = J.T;
 
-    unsigned char* base = smem_raw + (size_t)warp * js.smem_per_warp;
     // prefetch slots (PF only): lane l copies, and later reads, the data of its own point only
     cx<R>* pf_w = reinterpret_cast<cx<R>*>(base);               // [32]    w (DCF)
     R* pf_u = reinterpret_cast<R*>(pf_w + 32);                  // [32][2] fractional offsets
@@ -290,9 +285,22 @@ __global__ void __launch_bounds__(128, spread2d_pair<R, MM, BOPT>() ? 5 : 1)
     while (r0 < P) flush_row();
 }
 
-// register-row spreading for d = 2 when every job has the same m (2..8) and P <= 32
 template <class R, int MM, bool BOPT, bool PF>
-static infft_status launch_spread2d_m(JobSet<R>& js, cudaStream_t st) {
+// the paired form holds 2 (2m + 1) complex accumulators: at most 96 registers, so five 4-warp
+// blocks (20 warps) share an SM (the one-point form ran six at 80 registers)
+__global__ void __launch_bounds__(128, spread2d_pair<R, MM, BOPT>() ? 5 : 1)
+    k_spread2d(const __grid_constant__ JobSet<R> js) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    const int gitem = blockIdx.x * js.wpb + warp;
+    if (gitem >= js.pre_items[js.njobs]) return;
+    spread2d_item<R, MM, BOPT, PF>(js, gitem, smem_raw + (size_t)warp * js.smem_per_warp);
+}
+
+// Per-launch setup of the register-row spread: shared memory per warp (js.smem_per_warp), four
+// warps per block (js.wpb), and the jobs' common window polynomial in the parameter block.
+template <class R, int MM, bool BOPT, bool PF>
+static void spread2d_setup(JobSet<R>& js) {
     constexpr int W = 2 * MM + 1;
     constexpr int WE = spread2d_we<R, MM, BOPT>();
     size_t spw = spread2d_slot_bytes<R, PF>() + 32 * WE * sizeof(cx<R>) + 32 * spread2d_pitch<R, MM, BOPT>() * sizeof(R) + 96 * sizeof(int) + 32 * sizeof(cx<R>) +
@@ -312,6 +320,13 @@ static infft_status launch_spread2d_m(JobSet<R>& js, cudaStream_t st) {
     spw = (spw + 15) & ~(size_t)15;
     js.smem_per_warp = (int)spw;
     js.wpb = 4;
+}
+
+// register-row spreading for d = 2 when every job has the same m (2..8) and P <= 32
+template <class R, int MM, bool BOPT, bool PF>
+static infft_status launch_spread2d_m(JobSet<R>& js, cudaStream_t st) {
+    spread2d_setup<R, MM, BOPT, PF>(js);
+    const size_t spw = (size_t)js.smem_per_warp;
     const int nitems = js.pre_items[js.njobs];
     if (nitems == 0) return INFFT_OK;
     const size_t smem = spw * js.wpb;
