@@ -739,6 +739,21 @@ def run_single(args, rank, world, dist):
         fft_bytes = cbytes * G + cbytes * K                            # ideal single pass
         gbs = {"spread": spread_bytes / (st["spread"] / 1e3) / 1e9,
                "fft_total": fft_bytes / (sum(st["fft"]) / 1e3) / 1e9}
+        # every stage against HBM: the merge reads the padded tiles once (P = T + 2m per edge, the
+        # library's default tile edge) and writes the grid; FFT pass t reads Ms^(d-t) M^t and
+        # writes Ms^(d-t-1) M^(t+1) elements
+        T_def = min(256, p.Ms) if d == 1 else (16 if d == 2 else 8)
+        merge_bytes = p.work_items * (T_def + 2 * m) ** d * cbytes + cbytes * G
+        stage_roof = {"spread": {"bytes": int(spread_bytes), "ms": st["spread"]}}
+        if st["merge"] > 4e-3:
+            stage_roof["merge"] = {"bytes": int(merge_bytes), "ms": st["merge"]}
+        for t_ in range(d):
+            nb = cbytes * (p.Ms ** (d - t_) * M ** t_ + p.Ms ** (d - t_ - 1) * M ** (t_ + 1))
+            stage_roof[f"fft_pass{t_ + 1}"] = {"bytes": int(nb), "ms": st["fft"][t_]}
+        pk, _ = measured_peak()
+        for v_ in stage_roof.values():
+            v_["achieved"] = v_["bytes"] / (v_["ms"] / 1e3) / 1e9 if v_["ms"] > 0 else None
+            v_["frac"] = v_["achieved"] / pk if v_["achieved"] else None
         # plain and end to end
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -774,7 +789,8 @@ def run_single(args, rank, world, dist):
         rec = {"recon_per_s": world * args.steps / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
                "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
                "plain_recon_per_s": plain_rate, "e2e_recon_per_s": world / statistics.median(e2e),
-               "stage_ms": st, "stage_GBps": gbs, "spread_algorithmic_bytes": int(spread_bytes),
+               "stage_ms": st, "stage_GBps": gbs, "stage_roofline": stage_roof,
+               "spread_algorithmic_bytes": int(spread_bytes),
                "rel_err_vs_O1": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
                "O1_sampled_k": int(len(ks)), "O1_seconds": oracle_s,
                "weights": {"seconds": t_w, "cg_iters": info["iters"], "residual_inf": info["residual_inf"]},
@@ -803,6 +819,7 @@ def run_single(args, rank, world, dist):
         "roofline": {"bound": "hbm", "kernel": "spread", "achieved": head["stage_GBps"]["spread"], "peak": peak,
                      "unit": "GB/s", "frac": head["stage_GBps"]["spread"] / peak, "traffic": None,
                      "peak_kind": peak_kind, "algorithmic_bytes": head["spread_algorithmic_bytes"]},
+        "stage_roofline": head["stage_roofline"],
         "e2e": {"value": head["e2e_recon_per_s"], "unit": "recon/s",
                 "h2d_bytes_per_step": head["h2d_bytes_per_step"], "d2h_bytes_per_step": head["d2h_bytes_per_step"]},
         "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
