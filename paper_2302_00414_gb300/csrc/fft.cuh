@@ -62,7 +62,9 @@ __device__ __forceinline__ void fft_block(const JobSet<R>& js, const int pass, c
     const long long B = expl ? js.axB : ipow(M, D - 1 - t);
     const int MB = expl ? M / js.axblk : M;   // output block along the middle index
     const int n = Ms;
-    const int ns = n + (n >> 4);    // skewed line stride
+    // skewed line stride, odd in 8-byte words: the same element of 16 consecutive lines (the
+    // loads and stores of the passes along y and z) falls into 16 distinct bank pairs
+    const int ns = n + (n >> 4) + 1;
     const int logn = 31 - __clz(n);
     const long long nlines = A * B;
     const long long q0 = (long long)lb * L;
@@ -328,7 +330,7 @@ inline size_t fft_smem_mrg(const JobSet<R>& js) {
     for (int j = 0; j < js.njobs; ++j) {
         const Job<R>& J = js.job[j];
         const int n = J.Ms, L = fft_lines(n, (int)sizeof(cx<R>));
-        mx = std::max(mx, ((size_t)L * (n + n / 16) + n / 2) * sizeof(cx<R>) +
+        mx = std::max(mx, ((size_t)L * (n + n / 16 + 1) + n / 2) * sizeof(cx<R>) +
                               (size_t)mrg_tile_rows(L, J.T) * J.ntile * sizeof(int2) + (size_t)J.M * sizeof(R));
     }
     return mx;
@@ -341,7 +343,7 @@ inline size_t fft_smem(const JobSet<R>& js) {
     size_t mx = 0;
     for (int j = 0; j < js.njobs; ++j) {
         const int n = js.job[j].Ms, L = fft_lines(n, (int)sizeof(cx<R>));
-        mx = std::max(mx, ((size_t)L * (n + n / 16) + n / 2) * sizeof(cx<R>) + (size_t)js.job[j].M * sizeof(R));
+        mx = std::max(mx, ((size_t)L * (n + n / 16 + 1) + n / 2) * sizeof(cx<R>) + (size_t)js.job[j].M * sizeof(R));
     }
     return mx;
 }
