@@ -202,10 +202,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def profiled(name: str = "k_spread2d_batched_d2_m4.md"):
+def profiled(name: str = "k_spread2d_batched_d2_m4.md", kernel: str = None):
     """Figures of the committed ncu summary of the spreading kernel (keys "dram_bytes_per_launch",
     "smem_pipe_frac"), or {} when the kernel sources changed since that capture (hash
-    mismatch): a stale capture is not reported."""
+    mismatch) or the summary covers another instantiation than `kernel`: a stale capture is not
+    reported."""
     import hashlib
     summary = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(summary):
@@ -214,13 +215,17 @@ def profiled(name: str = "k_spread2d_batched_d2_m4.md"):
     for f in ("spread2d.cuh", "common.cuh", "jobset.cuh"):
         with open(os.path.join(ROOT, "paper_2302_00414_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    want, out = None, {}
+    want, out, captured = None, {}, None
     for line in open(summary):
         if line.startswith("source_sha256:"):
             want = line.split(":", 1)[1].strip()
+        if line.startswith("kernel:"):
+            captured = line.split(":", 1)[1].strip()
         for key in ("dram_bytes_per_launch", "smem_pipe_frac"):
             if line.startswith(key + ":"):
                 out[key] = float(line.split(":", 1)[1].strip())
+    if kernel is not None and captured != kernel:
+        return {}
     return out if want == h.hexdigest()[:16] else {}
 
 
@@ -432,7 +437,9 @@ def run_ours(args, rank, world, dist):
     spread_flops = Ntot * ((2 * 4 + 1) ** 2 * 4 + 2 * (2 * 4 + 1) * 2 * 10)
     peak, peak_kind = measured_peak()
     achieved = spread_bytes / (spread_ms / 1e3) / 1e9
-    prof = profiled()
+    # the paired register-row spread, with or without the prefetching copies as tuned
+    spread_kernel = "k_spread2d<float, 4, 0, %d>" % (0 if (tune_cfg or {}).get("prefetch") == 2 else 1)
+    prof = profiled(kernel=spread_kernel)
     # merge and the two FFT passes: bytes of the tensors they read and write (the padded
     # tiles as written by the spread), against their event-timed stage
     tile = ((tune_cfg or {}).get("tile") or 16)
@@ -613,7 +620,7 @@ def run_ours(args, rank, world, dist):
         "plain": {"value": plain_rate, "unit": "recon/s"}, "vs_plain": recon_per_s / world / plain_rate,
         "rel_err_vs_fp64": max(rel_errs) if rel_errs else None,
         "stage_ms": {"spread": spread_ms, "merge": merge_ms, "fft": fft_ms},
-        "roofline": {"bound": "smem", "kernel": "k_spread2d<float, 4, 0, 1>", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "smem", "kernel": spread_kernel, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
                      "traffic": int(prof["dram_bytes_per_launch"]) if "dram_bytes_per_launch" in prof else None,
                      "peak_kind": peak_kind, "algorithmic_bytes": int(spread_bytes),

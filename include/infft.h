@@ -132,8 +132,8 @@ infft_status infft_plan(int d, int M, int64_t N, const double* x, double sigma, 
  *               spread of d = 2 needs T + 2m + 1 <= 32 and the fused merge-FFT kernel T in
  *               {8, 16}); default 16 for d = 2, 8 for d = 3, min(256, M_sigma) for d = 1.
  *   item_cap  : most points per work item, >= 1 (default 512; 32 for d = 1).
- *   branches  : concurrent branches of batched adjoints whose first plan is this one (1..8;
- *               default 3 with device buffers, 8 with host buffers).
+ *   branches  : concurrent branches of batched adjoints with device buffers whose first plan
+ *               is this one (1..8; default 3; batches with host buffers keep 8).
  *   prefetch  : spreading kernels copy the next points' data to shared memory while they
  *               spread the current ones: 1 on, 2 off (default: by form and grid size).
  *   fused_fft : d = 2 adjoints merge the padded tiles and run both FFT passes in one

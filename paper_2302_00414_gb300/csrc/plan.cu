@@ -866,7 +866,9 @@ static infft_status run_batched(const infft_plan_t* plans, int count, int mode, 
 // The environment variable INFFT_BATCH_BRANCHES (1..8) overrides both.
 static int branch_count(const infft_plan_t* plans, int count, bool host_buffers = false) {
     int G = host_buffers ? 8 : 3;
-    if (plans[0]->tune.branches > 0) G = plans[0]->tune.branches;
+    // a plan's tuned count is for device buffers (the copies of host-buffer batches gain from
+    // more branches than the kernels alone)
+    if (!host_buffers && plans[0]->tune.branches > 0) G = plans[0]->tune.branches;
     else if (const char* env = getenv("INFFT_BATCH_BRANCHES")) G = std::max(1, std::min(8, atoi(env)));
     return std::max(1, std::min(G, count));
 }
