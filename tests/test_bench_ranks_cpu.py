@@ -79,3 +79,32 @@ def test_oracle_sample_keeps_the_batch_mix():
         assert all(Ms.count(M) == 4 for M in set(Ms))
         seen.update(pick)
     assert seen == set(range(len(sets)))
+
+
+def test_profiled_figures_only_for_the_captured_kernel(tmp_path, monkeypatch):
+    """The bench cites the committed ncu summary of the spread (DRAM traffic, shared-memory pipe)
+    only while the kernel sources hash as at the capture and the summary names the instantiation
+    the bench runs; otherwise it reports nothing rather than stale counters."""
+    import hashlib
+    import bench
+    h = hashlib.sha256()
+    for f in ("spread2d.cuh", "common.cuh", "jobset.cuh"):
+        with open(os.path.join(bench.ROOT, "paper_2302_00414_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    good = h.hexdigest()[:16]
+    prof_dir = tmp_path / "profiles"
+    prof_dir.mkdir()
+    def write(sha, kernel):
+        (prof_dir / "s.md").write_text(f"kernel: {kernel}\nsource_sha256: {sha}\n"
+                                       "dram_bytes_per_launch: 1000\nsmem_pipe_frac: 0.5\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    # the sources are read from the real tree: point ROOT's csrc at it through a link
+    os.symlink(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2302_00414_gb300"),
+               tmp_path / "paper_2302_00414_gb300")
+    write(good, "k_spread2d<float, 4, 0, 0>")
+    assert bench.profiled("s.md", kernel="k_spread2d<float, 4, 0, 0>") == {"dram_bytes_per_launch": 1000.0,
+                                                                            "smem_pipe_frac": 0.5}
+    assert bench.profiled("s.md", kernel="k_spread2d<float, 4, 0, 1>") == {}
+    write("0" * 16, "k_spread2d<float, 4, 0, 0>")
+    assert bench.profiled("s.md", kernel="k_spread2d<float, 4, 0, 0>") == {}
+
