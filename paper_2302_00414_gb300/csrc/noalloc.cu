@@ -117,8 +117,9 @@ infft_status run(infft_plan_s* p, int mode, const void* f, void* fhat, cudaStrea
     job.tmp1 = t1 ? reinterpret_cast<cx<R>*>(s + b_pad + b_grid) : nullptr;
     job.tmp2 = t2 ? reinterpret_cast<cx<R>*>(s + b_pad + b_grid + b_t1) : nullptr;
     // Every scratch cell is written before it is read (the spread stores whole padded
-    // tiles, the merge every grid cell, each FFT pass its whole output), so nothing left
-    // by an earlier call needs clearing.
+    // tiles, the merge every grid cell where a separate merge runs, each FFT pass its whole
+    // output; for d = 2 the first pass reads the padded tiles directly and the grid is not
+    // used), so nothing left by an earlier call needs clearing.
     return infft::run_jobs<R>(&job, 1, st, false, nullptr);
 }
 
