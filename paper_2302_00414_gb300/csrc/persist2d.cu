@@ -10,8 +10,8 @@
 // queue is a list of segments (a run of spread units, or one job's x or y blocks) in the kernel
 // parameters.
 //
-// Measured on the batched d = 2 workload (64 sets): 0.470 ms per step against 0.450 ms for the
-// staged kernels in three graph branches.  The FFT blocks run as four-warp CTAs at the spread's
+// Measured on the batched d = 2 workload (64 sets): 0.456 ms per step against 0.439 ms for the
+// staged kernels in graph branches.  The FFT blocks run as four-warp CTAs at the spread's
 // occupancy (five per SM), where the staged passes run eight-warp blocks at six per SM, and
 // the overlap does not make up for it.  The form is therefore taken only on request
 // (INFFT_PERSISTENT=1).
