@@ -23,16 +23,21 @@ namespace infft {
 // The z-planes of the shared tile are PZ >= P^2 cells apart with PZ = W (mod 16), so the
 // cells of 16 consecutive pairs, at q + const (mod 16) in 8-byte units, fall into
 // distinct bank pairs: no bank conflicts.  The tile is written out densely (P^3).
-// With PF the sorted data of the next 32 points (perm, cell, u, w) are copied to shared
+// With PF the sorted data of the next chunk of points (perm, cell, u, w) are copied to shared
 // memory with cp.async while the current ones are spread: with five warps per SM, other
 // warps cannot hide the staging's global loads.
 __host__ __device__ constexpr int spread3d_plane(int P, int W) { return P * P + (((W - P * P) % 16) + 16) % 16; }
 constexpr int SPREAD3D_T = 8;
 
-// bytes of the per-warp prefetch slots (w, u triples, perm, cell of 32 points); a multiple of 16
-template <class R, bool PF>
+// points staged per chunk: 16 for float32 with m <= 4, so that a warp's tile and staging fit
+// six warps in an SM's shared memory (with 32 they fit five); 32 otherwise
+template <class R, int MM>
+__host__ __device__ constexpr int spread3d_chunk() { return (sizeof(R) == 4 && MM <= 4) ? 16 : 32; }
+
+// bytes of the per-warp prefetch slots (w, u triples, perm, cell of a chunk); a multiple of 16
+template <class R, int MM, bool PF>
 __host__ __device__ constexpr size_t spread3d_slot_bytes() {
-    return PF ? 32 * (sizeof(cx<R>) + 3 * sizeof(R) + 2 * sizeof(int)) : 0;
+    return PF ? spread3d_chunk<R, MM>() * (sizeof(cx<R>) + 3 * sizeof(R) + 2 * sizeof(int)) : 0;
 }
 
 template <class R, int MM, bool PF>
@@ -44,6 +49,7 @@ __global__ void __launch_bounds__(64) k_spread3d(const __grid_constant__ JobSet<
     constexpr int P = T + 2 * MM, P2 = P * P;   // the padded edge of window modes
     constexpr int PZ = spread3d_plane(P, W), SC = P * PZ;
     constexpr bool F32 = sizeof(R) == 4;
+    constexpr int CH = spread3d_chunk<R, MM>();
     using V2 = typename std::conditional<F32, float2, double2>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -57,16 +63,16 @@ __global__ void __launch_bounds__(64) k_spread3d(const __grid_constant__ JobSet<
 
     unsigned char* base = smem_raw + (size_t)warp * js.smem_per_warp;
     // prefetch slots (PF only): lane l copies, and later reads, the data of its own point only
-    cx<R>* pf_w = reinterpret_cast<cx<R>*>(base);                      // [32]    w (DCF)
-    R* pf_u = reinterpret_cast<R*>(pf_w + 32);                         // [32][3] fractional offsets
-    int* pf_perm = reinterpret_cast<int*>(pf_u + 96);                  // [32]    caller's index
-    uint32_t* pf_cell = reinterpret_cast<uint32_t*>(pf_perm + 32);     // [32]    base cell
-    V2* pad = reinterpret_cast<V2*>(base + spread3d_slot_bytes<R, PF>());  // [P][PZ]
-    V2* cyv = pad + ((SC + 1) & ~1);                                   // [32][WE] c_j psi_y
-    R* psz = reinterpret_cast<R*>(cyv + 32 * WE);                      // [32][WE]
-    R* psx = psz + 32 * WE;                                            // [32][WE]
-    int* meta = reinterpret_cast<int*>(psx + 32 * WE);                 // [32] base cell in the shared tile
-    float* poly = reinterpret_cast<float*>(meta + 32);                 // window polynomial (float32 plans)
+    cx<R>* pf_w = reinterpret_cast<cx<R>*>(base);                      // [CH]    w (DCF)
+    R* pf_u = reinterpret_cast<R*>(pf_w + CH);                         // [CH][3] fractional offsets
+    int* pf_perm = reinterpret_cast<int*>(pf_u + 3 * CH);              // [CH]    caller's index
+    uint32_t* pf_cell = reinterpret_cast<uint32_t*>(pf_perm + CH);     // [CH]    base cell
+    V2* pad = reinterpret_cast<V2*>(base + spread3d_slot_bytes<R, MM, PF>());  // [P][PZ]
+    V2* cyv = pad + ((SC + 1) & ~1);                                   // [CH][WE] c_j psi_y
+    R* psz = reinterpret_cast<R*>(cyv + CH * WE);                      // [CH][WE]
+    R* psx = psz + CH * WE;                                            // [CH][WE]
+    int* meta = reinterpret_cast<int*>(psx + CH * WE);                 // [CH] base cell in the shared tile
+    float* poly = reinterpret_cast<float*>(meta + CH);                 // window polynomial (float32 plans)
     const bool use_poly = F32 && J.wpoly != nullptr;
     if (use_poly) {
         for (int e = lane; e < (WPOLY_DEG + 1) * wpoly_stride(W); e += 32) poly[e] = J.wpoly[e];
@@ -92,8 +98,8 @@ __global__ void __launch_bounds__(64) k_spread3d(const __grid_constant__ JobSet<
         for (int s = 0; s < W; ++s) { v[r][s].x = R(0); v[r][s].y = R(0); }
     int cur = -1;
     const bool dcf = J.mode == INFFT_MODE_DCF;
-    auto prefetch = [&](int c) {   // the sorted data of points c .. c + 31 of the item
-        if (c + lane < item.z) {
+    auto prefetch = [&](int c) {   // the sorted data of points c .. c + CH - 1 of the item
+        if (lane < CH && c + lane < item.z) {
             const size_t i = (size_t)item.y + c + lane;
             cp_async<4>(pf_perm + lane, J.perm + i);
             cp_async<4>(pf_cell + lane, J.cell + i);
@@ -105,8 +111,8 @@ __global__ void __launch_bounds__(64) k_spread3d(const __grid_constant__ JobSet<
     };
     if (PF && item.z > 0) prefetch(0);
 
-    for (int c0 = 0; c0 < item.z; c0 += 32) {
-        const int np = min(32, item.z - c0);
+    for (int c0 = 0; c0 < item.z; c0 += CH) {
+        const int np = min(CH, item.z - c0);
         __syncwarp();
         if (PF) cp_async_wait_all();
         if (lane < np) {
@@ -148,7 +154,7 @@ __global__ void __launch_bounds__(64) k_spread3d(const __grid_constant__ JobSet<
             }
         }
         __syncwarp();   // orders every read of the prefetch slots before their refill
-        if (PF && c0 + 32 < item.z) prefetch(c0 + 32);
+        if (PF && c0 + CH < item.z) prefetch(c0 + CH);
         for (int p = 0; p < np; ++p) {
             const int b0 = meta[p];
             if (b0 != cur) {   // uniform across the warp
@@ -207,9 +213,10 @@ static infft_status launch_spread3d_m(JobSet<R>& js, cudaStream_t st) {
     constexpr int WE = W + 1;
     constexpr int P = SPREAD3D_T + 2 * MM;
     const size_t cells = (size_t)P * spread3d_plane(P, W);
-    size_t spw = spread3d_slot_bytes<R, PF>() +
-                 ((cells + 1) & ~(size_t)1) * sizeof(cx<R>) + 32 * WE * (sizeof(cx<R>) + 2 * sizeof(R)) +
-                 32 * sizeof(int) + (WPOLY_DEG + 1) * wpoly_stride(W) * sizeof(float);
+    constexpr int CH = spread3d_chunk<R, MM>();
+    size_t spw = spread3d_slot_bytes<R, MM, PF>() +
+                 ((cells + 1) & ~(size_t)1) * sizeof(cx<R>) + CH * WE * (sizeof(cx<R>) + 2 * sizeof(R)) +
+                 CH * sizeof(int) + (WPOLY_DEG + 1) * wpoly_stride(W) * sizeof(float);
     spw = (spw + 15) & ~(size_t)15;
     const size_t smem_cap = 200 * 1024;
     if (spw > smem_cap) {
@@ -222,6 +229,9 @@ static infft_status launch_spread3d_m(JobSet<R>& js, cudaStream_t st) {
     if (nitems == 0) return INFFT_OK;
     const size_t smem = spw * js.wpb;
     INFFT_CUDA(cudaFuncSetAttribute(k_spread3d<R, MM, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // the tiles bound the warps per SM: ask for all of the SM's unified memory as shared memory
+    INFFT_CUDA(cudaFuncSetAttribute(k_spread3d<R, MM, PF>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    (int)cudaSharedmemCarveoutMaxShared));
     k_spread3d<R, MM, PF><<<(nitems + js.wpb - 1) / js.wpb, 32 * js.wpb, smem, st>>>(js);
     INFFT_LAUNCHED();
     return INFFT_OK;
