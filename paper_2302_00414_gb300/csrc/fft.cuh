@@ -2,6 +2,8 @@
 // 1-2): the block body shared by the FFT kernels of nfft.cu and the persistent d = 2 adjoint.
 #pragma once
 
+#include <algorithm>
+
 #include "jobset.cuh"
 #include "spread.cuh"
 
@@ -45,6 +47,7 @@ __host__ __device__ inline int mrg_tile_rows(int L, int T) { return (L <= T ? 1 
 // from the padded tiles as they are loaded: the halo merge of k_merge2d in the same order per
 // cell, with no grid written or read in between.  The item ranges of the tiles the block's
 // rows draw on are staged in shared memory after the twiddles first.
+//
 // One block's lines of FFT pass `pass` (block gblk of the pass, global over the JobSet's jobs),
 // with the block's dynamic shared memory at smem_raw: the body of k_fft, and the FFT units of the
 // persistent d = 2 kernel.  Generic in the block size (a power of two, >= 32).
